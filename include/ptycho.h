@@ -1,0 +1,158 @@
+/*
+ * libptycho: multislice ptychography loss and image gradient on one GB300 GPU.
+ *
+ * The library evaluates the amplitude cost of Eq. 1 (Sec. II-B),
+ *     F = sum_i sum_k ( sqrt(I_i[k]) - |G(P, O)_i[k]| )^2,
+ * where G is the multislice model of Sec. II-B (each slice transmits the
+ * wave, which is then Fourier transformed, multiplied by the Fresnel
+ * propagator and inverse transformed before the next slice; the exit wave is
+ * Fourier transformed to the detector), together with its exact gradient,
+ * which by Eq. 2 (Sec. III) is the sum of per-position gradients, each
+ * supported on its own probe window.
+ *
+ * Conventions (fixed, not options):
+ *   - complex numbers are interleaved float pairs (re, im), i.e. complex64;
+ *   - 2-D FFTs are orthonormal with forward kernel exp(-2 pi i k.n / M); the
+ *     far field and the measurements are in FFT order (DC at [0][0]);
+ *   - the Fresnel propagator between consecutive slices is
+ *     h(ky, kx) = exp(-i pi lambda dz (ky^2 + kx^2)), k = fftfreq(M, pixel)
+ *     in 1/Angstrom, applied S-1 times for S slices;
+ *   - one probe P [M][M] is shared by all positions; position i is the
+ *     integer top-left corner (y_i, x_i) of its M x M window in the object,
+ *     with 0 <= y_i <= H-M and 0 <= x_i <= W-M (no wrap-around);
+ *   - gradients are g = dF/dRe + i dF/dIm (PyTorch's convention), written
+ *     (overwritten, never accumulated) into caller-owned buffers;
+ *   - where |Psi| = 0 the amplitude's subgradient Psi/|Psi| is taken as 0.
+ *
+ * Memory: every array argument is caller-owned and must be CUDA device
+ * memory (cudaMalloc / PyTorch), except where an argument says a host
+ * pointer is accepted.  The plan owns only its tables and its workspace;
+ * nothing is freed across this interface.
+ *
+ * Streams: work is enqueued on the stream given to each call (NULL = the
+ * legacy default stream) and runs asynchronously unless stated otherwise;
+ * outputs are valid once that stream has been synchronised.
+ *
+ * Errors: every entry point returns PTYCHO_OK (0) or a negative code and
+ * records a message retrievable with ptycho_last_error() (per host thread).
+ */
+#ifndef PTYCHO_H_
+#define PTYCHO_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PTYCHO_API __attribute__((visibility("default")))
+#else
+#define PTYCHO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTYCHO_OK              0
+#define PTYCHO_ERR_ARG        -1  /* null pointer, bad shape or parameter */
+#define PTYCHO_ERR_POSITION   -2  /* a probe window lies outside the object */
+#define PTYCHO_ERR_CUDA       -3  /* a CUDA runtime call failed */
+#define PTYCHO_ERR_NOMEM      -4  /* workspace allocation failed */
+#define PTYCHO_ERR_TIMEOUT    -5  /* a bounded device-side wait gave up */
+#define PTYCHO_ERR_UNSUPPORTED -6 /* probe window size not supported */
+
+#define PTYCHO_FP32    0   /* all bulk complex arithmetic in FP32 */
+
+/* Flags for ptycho_params.flags */
+#define PTYCHO_FLAG_ASYNC_CHECK 1  /* do not synchronise to validate positions
+                                      on the host; out-of-range windows are
+                                      skipped on the device and reported by
+                                      ptycho_plan_status() */
+
+typedef struct {
+  float re, im;
+} ptycho_c64;
+
+/* Problem description (Sec. II-B, Eq. 1).  Windows M in {64, 128}. */
+typedef struct {
+  int32_t M;          /* probe window / detector side, pixels */
+  int32_t S;          /* number of object slices */
+  int32_t H, W;       /* object height and width, pixels */
+  int32_t N;          /* number of probe positions per call */
+  double lambda_A;    /* wavelength, Angstrom */
+  double dz_A;        /* slice spacing, Angstrom */
+  double pixel_A;     /* real-space pixel, Angstrom */
+  int32_t precision;  /* PTYCHO_FP32 */
+  int32_t flags;      /* PTYCHO_FLAG_* */
+  int64_t workspace_bytes; /* cap on the plan's workspace; 0 = 8 GiB.  Positions
+                              are processed in chunks that fit the cap, so the
+                              memory used does not grow with N. */
+  int32_t tile_h, tile_w;  /* object-gradient accumulation tile (pixels);
+                              0 = 64 x 64.  tile_h * tile_w <= 8192. */
+} ptycho_params;
+
+typedef struct ptycho_plan_s* ptycho_plan;
+
+/* Create a plan: validates *params, computes the FFT twiddles and the
+ * Fresnel propagator in FP64 on the host, uploads them as FP32 tables and
+ * allocates the workspace.  The caller's current CUDA device is used.
+ * Returns PTYCHO_ERR_ARG / _UNSUPPORTED / _NOMEM / _CUDA on failure, in which
+ * case *plan is set to NULL. */
+PTYCHO_API int ptycho_plan_create(ptycho_plan* plan, const ptycho_params* params);
+
+/* Release the plan's tables and workspace (synchronises the device). */
+PTYCHO_API int ptycho_plan_destroy(ptycho_plan plan);
+
+/* Number of positions processed per chunk and workspace bytes held. */
+PTYCHO_API int ptycho_plan_info(ptycho_plan plan, int32_t* chunk_positions, int64_t* workspace_bytes);
+
+/* Device-side status of the most recent call on this plan (after the stream
+ * has been synchronised): PTYCHO_OK or PTYCHO_ERR_POSITION.  Clears it. */
+PTYCHO_API int ptycho_plan_status(ptycho_plan plan);
+
+/* Forward model G (Sec. II-B) for all N positions.
+ *   pos_yx     int32 [N][2]   device, (y, x) window corners
+ *   probe      c64   [M][M]   device
+ *   obj        c64   [S][H][W] device, slice transmissions O_s
+ *   psi_out    c64   [N][M][M] device or NULL: orthonormal far field, FFT order
+ *   intens_out f32   [N][M][M] device or NULL: |psi_out|^2
+ * At least one output must be non-NULL. */
+PTYCHO_API int ptycho_forward(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe,
+                   const ptycho_c64* obj, ptycho_c64* psi_out, float* intens_out,
+                   void* stream);
+
+/* Cost of Eq. 1 and its gradients (Eq. 2).
+ *   meas_I     f32 [N][M][M] device, measured intensities (>= 0), FFT order
+ *   loss_out   double[1], device or host pointer: F, accumulated in FP64.
+ *              For a host pointer the call synchronises the stream.
+ *   grad_obj   c64 [S][H][W] device or NULL: dF/dO (overwritten; zero outside
+ *              every window)
+ *   grad_probe c64 [M][M] device or NULL: dF/dP (overwritten)
+ * Deterministic: the same inputs give bit-identical outputs (fixed-order
+ * reductions, no atomics). */
+PTYCHO_API int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe,
+                     const ptycho_c64* obj, const float* meas_I, double* loss_out,
+                     ptycho_c64* grad_obj, ptycho_c64* grad_probe, void* stream);
+
+/* One full-batch gradient-descent step (Sec. II-B update rule, applied to the
+ * position sum of Eq. 2): O <- O - t alpha_obj dF/dO, P <- P - t alpha_probe dF/dP,
+ * in place.  line_search = 0: t = 1.  line_search = 1: Armijo backtracking,
+ * t = 1, 1/2, ... (at most 20 halvings) until
+ *   F(new) <= F(old) - 1e-4 t (alpha_obj |dF/dO|^2 + alpha_probe |dF/dP|^2),
+ * else t = 0 (inputs unchanged).  The scalars are FP64; the line search reads
+ * them on the host and therefore synchronises the stream.
+ *   loss_out   double[1] device or host, or NULL: F before the step
+ *   t_out      double[1] host, or NULL: the accepted t */
+PTYCHO_API int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj,
+                const float* meas_I, double alpha_obj, double alpha_probe,
+                int32_t line_search, double* loss_out, double* t_out, void* stream);
+
+/* Text of the last error on the calling host thread ("" if none). */
+PTYCHO_API const char* ptycho_last_error(void);
+
+/* Library version string. */
+PTYCHO_API const char* ptycho_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTYCHO_H_ */

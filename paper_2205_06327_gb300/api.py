@@ -1,0 +1,170 @@
+"""PyTorch-facing wrapper of libptycho (the C-ABI in include/ptycho.h).
+
+PyTorch supplies device memory and streams; every step of the computation
+runs in the library's CUDA kernels.  Tensors:
+
+* ``pos``   int32  [N, 2] (y, x) top-left window corners
+* ``probe`` complex64 [M, M]
+* ``obj``   complex64 [S, H, W] slice transmissions
+* ``meas``  float32 [N, M, M] measured intensities, FFT order
+
+Host (CPU) tensors are accepted and copied to the plan's device first; the
+results then come back to the host as well.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import PtychoParams, check
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+@dataclass
+class Geometry:
+    M: int
+    S: int
+    H: int
+    W: int
+    N: int
+    lambda_A: float = 0.0251
+    dz_A: float = 2.0
+    pixel_A: float = 0.1
+
+
+class Plan:
+    """A ``ptycho_plan``: tables and workspace for one problem shape."""
+
+    def __init__(self, geom: Geometry, device: torch.device | int | str = "cuda",
+                 workspace_bytes: int = 0, tile: tuple[int, int] = (0, 0), async_check: bool = False):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libptycho needs a CUDA device; there is no CPU fallback")
+        self.lib = _lib.load()
+        self.geom = geom
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        p = PtychoParams()
+        p.M, p.S, p.H, p.W, p.N = geom.M, geom.S, geom.H, geom.W, geom.N
+        p.lambda_A, p.dz_A, p.pixel_A = geom.lambda_A, geom.dz_A, geom.pixel_A
+        p.precision = _lib.PTYCHO_FP32
+        p.flags = _lib.PTYCHO_FLAG_ASYNC_CHECK if async_check else 0
+        p.workspace_bytes = int(workspace_bytes)
+        p.tile_h, p.tile_w = int(tile[0]), int(tile[1])
+        self._params = p
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.ptycho_plan_create(C.byref(h), C.byref(p)))
+        self._h = h
+
+    # ------------------------------------------------------------------ info
+    @property
+    def chunk(self) -> int:
+        c, w = C.c_int32(), C.c_int64()
+        check(self.lib.ptycho_plan_info(self._h, C.byref(c), C.byref(w)))
+        return c.value
+
+    @property
+    def workspace_bytes(self) -> int:
+        c, w = C.c_int32(), C.c_int64()
+        check(self.lib.ptycho_plan_info(self._h, C.byref(c), C.byref(w)))
+        return w.value
+
+    def status(self) -> None:
+        with torch.cuda.device(self.device):
+            check(self.lib.ptycho_plan_status(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            with torch.cuda.device(self.device):
+                self.lib.ptycho_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- helpers
+    def _dev(self, t: torch.Tensor, dtype: torch.dtype, shape: tuple, name: str) -> torch.Tensor:
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+        if t.device != self.device:
+            t = t.to(self.device, non_blocking=True)
+        return t.contiguous()
+
+    def _inputs(self, pos, probe, obj, meas=None):
+        g = self.geom
+        pos = self._dev(pos, torch.int32, (g.N, 2), "pos")
+        probe = self._dev(probe, torch.complex64, (g.M, g.M), "probe")
+        obj = self._dev(obj, torch.complex64, (g.S, g.H, g.W), "obj")
+        if meas is not None:
+            meas = self._dev(meas, torch.float32, (g.N, g.M, g.M), "meas")
+        return pos, probe, obj, meas
+
+    # ------------------------------------------------------------ operations
+    def forward(self, pos, probe, obj, want_psi: bool = True, want_intensity: bool = False):
+        """Far fields G(p, V) (Sec. II-B).  Returns (psi or None, intensity or None)."""
+        host = not probe.is_cuda
+        g = self.geom
+        pos, probe, obj, _ = self._inputs(pos, probe, obj)
+        psi = torch.empty((g.N, g.M, g.M), dtype=torch.complex64, device=self.device) if want_psi else None
+        inten = torch.empty((g.N, g.M, g.M), dtype=torch.float32, device=self.device) if want_intensity else None
+        with torch.cuda.device(self.device):
+            check(self.lib.ptycho_forward(self._h, _ptr(pos), _ptr(probe), _ptr(obj), _ptr(psi), _ptr(inten),
+                                          _stream_handle(self.device)))
+        if host:
+            psi = psi.cpu() if psi is not None else None
+            inten = inten.cpu() if inten is not None else None
+        return psi, inten
+
+    def loss_grad(self, pos, probe, obj, meas, want_obj: bool = True, want_probe: bool = True,
+                  out_obj: torch.Tensor | None = None, out_probe: torch.Tensor | None = None):
+        """(F, dF/dO, dF/dP) of Eq. 1 / Eq. 2.  F is a float64 0-d tensor on the device."""
+        host = not probe.is_cuda
+        g = self.geom
+        pos, probe, obj, meas = self._inputs(pos, probe, obj, meas)
+        gO = out_obj if out_obj is not None else (
+            torch.empty((g.S, g.H, g.W), dtype=torch.complex64, device=self.device) if want_obj else None)
+        gP = out_probe if out_probe is not None else (
+            torch.empty((g.M, g.M), dtype=torch.complex64, device=self.device) if want_probe else None)
+        loss = torch.empty((), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            check(self.lib.ptycho_loss_grad(self._h, _ptr(pos), _ptr(probe), _ptr(obj), _ptr(meas), _ptr(loss),
+                                            _ptr(gO), _ptr(gP), _stream_handle(self.device)))
+        if host:
+            return loss.cpu(), (gO.cpu() if gO is not None else None), (gP.cpu() if gP is not None else None)
+        return loss, gO, gP
+
+    def step(self, pos, probe: torch.Tensor, obj: torch.Tensor, meas, alpha_obj: float, alpha_probe: float,
+             line_search: bool = False):
+        """One full-batch gradient-descent step, in place on device tensors ``probe`` and ``obj``.
+
+        Returns (F before the step as a float64 device tensor, accepted step scale t)."""
+        if not (probe.is_cuda and obj.is_cuda and probe.is_contiguous() and obj.is_contiguous()):
+            raise ValueError("step updates probe and obj in place: pass contiguous device tensors")
+        pos, _, _, meas = self._inputs(pos, probe, obj, meas)
+        loss = torch.empty((), dtype=torch.float64, device=self.device)
+        t = C.c_double(0.0)
+        with torch.cuda.device(self.device):
+            check(self.lib.ptycho_step(self._h, _ptr(pos), _ptr(probe), _ptr(obj), _ptr(meas), float(alpha_obj),
+                                       float(alpha_probe), int(bool(line_search)), _ptr(loss), C.byref(t),
+                                       _stream_handle(self.device)))
+        return loss, t.value
+
+
+def version() -> str:
+    return _lib.load().ptycho_version().decode()

@@ -1,0 +1,66 @@
+// Declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ptycho {
+
+enum ChainMode { MODE_FORWARD = 0, MODE_LOSS = 1, MODE_GRAD = 2 };
+
+// Arguments of the per-position slice-chain kernel.  Positions
+// [pos_begin, pos_begin + n_pos) of the call are processed, one per block.
+struct ChainArgs {
+  const int2* pos;        // [N] (y, x)
+  int pos_begin;
+  int n_pos;
+  const float2* probe;    // [M][M]
+  const float2* obj;      // [S][H][W]
+  const float2* obj_dir;  // [S][H][W] or null: evaluate at obj + obj_step * obj_dir
+  const float2* probe_dir;// [M][M] or null: evaluate at probe + probe_step * probe_dir
+  float obj_step, probe_step;
+  const float* meas;      // [N][M][M] FFT order
+  int S, H, W;
+  const float2* tw;       // [M]   w_M^e = exp(-2 pi i e / M)
+  const float2* hs;       // [M]   one separable factor of the propagator, times 1/M
+  float2* ws_psi;         // [n_pos][S-1][M][M] waves entering slices 1..S-1
+  float2* ws_gphi;        // [n_pos][S][M][M]   gradient w.r.t. each slice's exit wave
+  float2* ws_gp;          // [n_pos][M][M]      per-position probe gradient
+  double* loss_part;      // [n_pos]
+  float2* psi_out;        // [N][M][M] or null (forward mode)
+  float* int_out;         // [N][M][M] or null (forward mode)
+  int* status;            // device error word (PTYCHO_ERR_POSITION on a bad window)
+};
+
+// chain_kernels.cu
+int chain_threads(int M);
+size_t chain_smem_bytes(int M);
+cudaError_t chain_prepare(int M);  // raise the dynamic shared-memory limit
+cudaError_t launch_chain(int M, ChainMode mode, const ChainArgs& a, cudaStream_t st);
+
+// reduce_kernels.cu
+struct AccumArgs {
+  const int2* pos;
+  int pos_begin, n_pos;
+  int M, S, H, W;
+  int tile_h, tile_w;
+  const float2* probe;      // wave entering slice 0 (= probe)
+  const float2* ws_psi;
+  const float2* ws_gphi;
+  float2* grad_obj;         // [S][H][W]
+  int accumulate;           // 0: overwrite the whole gradient, 1: add
+};
+cudaError_t launch_accum_obj_grad(const AccumArgs& a, cudaStream_t st);
+cudaError_t launch_probe_grad(const float2* ws_gp, int n_pos, int M, float2* part, int n_split,
+                              float2* grad_probe, int accumulate, cudaStream_t st);
+cudaError_t launch_loss_accum(const double* loss_part, int n, double* acc, int accumulate,
+                              cudaStream_t st);
+cudaError_t launch_axpy(float2* y, const float2* x, const float2* base, double alpha, size_t n,
+                        cudaStream_t st);  // y = base + alpha * x
+cudaError_t launch_norm2(const float2* x, size_t n, double* part, int n_part, double* out,
+                         int slot, cudaStream_t st);
+cudaError_t launch_check_positions(const int2* pos, int n, int M, int H, int W, int* status,
+                                   cudaStream_t st);
+
+}  // namespace ptycho

@@ -1,0 +1,449 @@
+// C-ABI of libptycho: plan management, argument validation and the host-side
+// orchestration of the per-chunk kernel sequence.  See include/ptycho.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ptycho.h"
+#include "internal.h"
+
+using namespace ptycho;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(PTYCHO_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr)                                 \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+constexpr int64_t kDefaultWorkspace = 8ll << 30;
+constexpr int kProbeSplit = 32;
+constexpr int kNormParts = 512;
+
+}  // namespace
+
+struct ptycho_plan_s {
+  ptycho_params p{};
+  int device = 0;
+  int sm_count = 0;
+  int chunk = 0;             // positions per chunk
+  int64_t ws_bytes = 0;
+  float2* d_tw = nullptr;     // [M]
+  float2* d_hs = nullptr;     // [M]
+  float2* ws_psi = nullptr;   // [chunk][S-1][M][M]
+  float2* ws_gphi = nullptr;  // [chunk][S][M][M]
+  float2* ws_gp = nullptr;    // [chunk][M][M]
+  float2* gp_part = nullptr;  // [kProbeSplit][M][M]
+  double* loss_part = nullptr;  // [chunk]
+  double* d_scal = nullptr;   // [8]: 0 loss, 1 |gO|^2, 2 |gP|^2, 3 trial loss
+  double* norm_part = nullptr;  // [kNormParts]
+  int* d_status = nullptr;
+  int* h_pos = nullptr;       // pinned, [N][2]
+  double* h_scal = nullptr;   // pinned, [8]
+  // gradient-descent step buffers (allocated on first use)
+  float2* g_obj = nullptr;
+  float2* g_probe = nullptr;
+};
+
+namespace {
+
+void free_plan(ptycho_plan pl) {
+  if (!pl) return;
+  cudaFree(pl->d_tw);
+  cudaFree(pl->d_hs);
+  cudaFree(pl->ws_psi);
+  cudaFree(pl->ws_gphi);
+  cudaFree(pl->ws_gp);
+  cudaFree(pl->gp_part);
+  cudaFree(pl->loss_part);
+  cudaFree(pl->d_scal);
+  cudaFree(pl->norm_part);
+  cudaFree(pl->d_status);
+  cudaFree(pl->g_obj);
+  cudaFree(pl->g_probe);
+  if (pl->h_pos) cudaFreeHost(pl->h_pos);
+  if (pl->h_scal) cudaFreeHost(pl->h_scal);
+  delete pl;
+}
+
+template <class T>
+int dev_alloc(T** p, size_t count, const char* what) {
+  if (count == 0) {
+    *p = nullptr;
+    return PTYCHO_OK;
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(PTYCHO_ERR_NOMEM, std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+  }
+  return PTYCHO_OK;
+}
+
+int validate_params(const ptycho_params& p) {
+  if (p.M != 64 && p.M != 128) return fail(PTYCHO_ERR_UNSUPPORTED, "probe window M must be 64 or 128");
+  if (p.S < 1) return fail(PTYCHO_ERR_ARG, "S must be >= 1");
+  if (p.H < p.M || p.W < p.M) return fail(PTYCHO_ERR_ARG, "object must be at least M x M");
+  if (p.N < 0) return fail(PTYCHO_ERR_ARG, "N must be >= 0");
+  if (p.precision != PTYCHO_FP32) return fail(PTYCHO_ERR_UNSUPPORTED, "precision must be PTYCHO_FP32");
+  if (!(p.pixel_A > 0) || !std::isfinite(p.lambda_A) || !std::isfinite(p.dz_A))
+    return fail(PTYCHO_ERR_ARG, "bad propagator parameters");
+  if (p.workspace_bytes < 0) return fail(PTYCHO_ERR_ARG, "workspace_bytes must be >= 0");
+  const int th = p.tile_h ? p.tile_h : 64, tw = p.tile_w ? p.tile_w : 64;
+  if (th < 1 || tw < 1 || th * tw > 8192) return fail(PTYCHO_ERR_ARG, "tile_h * tile_w must be in [1, 8192]");
+  if ((int64_t)p.S * p.H * p.W > (int64_t)1 << 34) return fail(PTYCHO_ERR_ARG, "object too large");
+  return PTYCHO_OK;
+}
+
+// Positions check on the host (pinned copy) unless the plan asks for the
+// asynchronous device-side check only.
+int check_positions(ptycho_plan pl, const int32_t* pos, cudaStream_t st) {
+  const ptycho_params& p = pl->p;
+  if (p.N == 0) return PTYCHO_OK;
+  if (!is_device_ptr(pos)) return fail(PTYCHO_ERR_ARG, "pos_yx must be a device pointer");
+  if (!aligned(pos, 8)) return fail(PTYCHO_ERR_ARG, "pos_yx must be 8-byte aligned");
+  if (p.flags & PTYCHO_FLAG_ASYNC_CHECK) return PTYCHO_OK;
+  CUDA_TRY(cudaMemcpyAsync(pl->h_pos, pos, sizeof(int32_t) * 2 * (size_t)p.N, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < p.N; ++i) {
+    const int y = pl->h_pos[2 * i], x = pl->h_pos[2 * i + 1];
+    if (y < 0 || x < 0 || y > p.H - p.M || x > p.W - p.M) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "position %d (y=%d, x=%d) puts the %dx%d window outside the %dx%d object", i, y, x,
+               p.M, p.M, p.H, p.W);
+      return fail(PTYCHO_ERR_POSITION, buf);
+    }
+  }
+  return PTYCHO_OK;
+}
+
+int check_array(const void* ptr, const char* name, bool required) {
+  if (!ptr) return required ? fail(PTYCHO_ERR_ARG, std::string(name) + " is NULL") : PTYCHO_OK;
+  if (!is_device_ptr(ptr)) return fail(PTYCHO_ERR_ARG, std::string(name) + " must be a device pointer");
+  if (!aligned(ptr, 8)) return fail(PTYCHO_ERR_ARG, std::string(name) + " must be 8-byte aligned");
+  return PTYCHO_OK;
+}
+
+ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, const ptycho_c64* obj,
+                    const float* meas) {
+  ChainArgs a{};
+  a.pos = reinterpret_cast<const int2*>(pos);
+  a.probe = reinterpret_cast<const float2*>(probe);
+  a.obj = reinterpret_cast<const float2*>(obj);
+  a.meas = meas;
+  a.S = pl->p.S;
+  a.H = pl->p.H;
+  a.W = pl->p.W;
+  a.tw = pl->d_tw;
+  a.hs = pl->d_hs;
+  a.ws_psi = pl->ws_psi;
+  a.ws_gphi = pl->ws_gphi;
+  a.ws_gp = pl->ws_gp;
+  a.loss_part = pl->loss_part;
+  a.status = pl->d_status;
+  return a;
+}
+
+// F (and optionally gradients) at (probe + probe_step*probe_dir, obj + obj_step*obj_dir);
+// the loss lands in pl->d_scal[slot].
+int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, const ptycho_c64* obj,
+                  const float* meas, float2* grad_obj, float2* grad_probe, int slot, const float2* obj_dir,
+                  float obj_step, const float2* probe_dir, float probe_step, cudaStream_t st) {
+  const ptycho_params& p = pl->p;
+  const bool want_grad = grad_obj || grad_probe;
+  if (p.N == 0) {
+    CUDA_TRY(cudaMemsetAsync(pl->d_scal + slot, 0, sizeof(double), st));
+    if (grad_obj) CUDA_TRY(cudaMemsetAsync(grad_obj, 0, sizeof(float2) * (size_t)p.S * p.H * p.W, st));
+    if (grad_probe) CUDA_TRY(cudaMemsetAsync(grad_probe, 0, sizeof(float2) * (size_t)p.M * p.M, st));
+    return PTYCHO_OK;
+  }
+  ChainArgs a = base_args(pl, pos, probe, obj, meas);
+  a.obj_dir = obj_dir;
+  a.obj_step = obj_step;
+  a.probe_dir = probe_dir;
+  a.probe_step = probe_step;
+  for (int c0 = 0, ci = 0; c0 < p.N; c0 += pl->chunk, ++ci) {
+    const int n = p.N - c0 < pl->chunk ? p.N - c0 : pl->chunk;
+    a.pos_begin = c0;
+    a.n_pos = n;
+    CUDA_TRY(launch_chain(p.M, want_grad ? MODE_GRAD : MODE_LOSS, a, st));
+    if (grad_obj) {
+      AccumArgs g{};
+      g.pos = a.pos;
+      g.pos_begin = c0;
+      g.n_pos = n;
+      g.M = p.M;
+      g.S = p.S;
+      g.H = p.H;
+      g.W = p.W;
+      g.tile_h = p.tile_h ? p.tile_h : 64;
+      g.tile_w = p.tile_w ? p.tile_w : 64;
+      g.probe = a.probe;
+      g.ws_psi = pl->ws_psi;
+      g.ws_gphi = pl->ws_gphi;
+      g.grad_obj = grad_obj;
+      g.accumulate = ci > 0;
+      CUDA_TRY(launch_accum_obj_grad(g, st));
+    }
+    if (grad_probe)
+      CUDA_TRY(launch_probe_grad(pl->ws_gp, n, p.M, pl->gp_part, kProbeSplit, grad_probe, ci > 0, st));
+    CUDA_TRY(launch_loss_accum(pl->loss_part, n, pl->d_scal + slot, ci > 0, st));
+  }
+  return PTYCHO_OK;
+}
+
+int deliver_loss(ptycho_plan pl, int slot, double* loss_out, cudaStream_t st) {
+  if (!loss_out) return PTYCHO_OK;
+  if (is_device_ptr(loss_out)) {
+    CUDA_TRY(cudaMemcpyAsync(loss_out, pl->d_scal + slot, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(pl->h_scal + slot, pl->d_scal + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    *loss_out = pl->h_scal[slot];
+  }
+  return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ptycho_last_error(void) { return g_last_error.c_str(); }
+
+const char* ptycho_version(void) { return "libptycho 0.1 (sm_103a, FP32 register-pass FFT chain)"; }
+
+int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
+  g_last_error.clear();
+  if (!out || !params) return fail(PTYCHO_ERR_ARG, "plan and params must be non-NULL");
+  *out = nullptr;
+  int rc = validate_params(*params);
+  if (rc) return rc;
+  ptycho_plan pl = new (std::nothrow) ptycho_plan_s;
+  if (!pl) return fail(PTYCHO_ERR_NOMEM, "host allocation failed");
+  pl->p = *params;
+  const ptycho_params& p = pl->p;
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
+  if ((e = chain_prepare(p.M)) != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+
+  // Tables in FP64 on the host, rounded once to FP32.
+  const int M = p.M;
+  std::vector<float2> tw(M), hs(M);
+  const double two_pi = 6.283185307179586476925287;
+  for (int k = 0; k < M; ++k) {
+    const double ang = -two_pi * (double)k / (double)M;
+    tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    // fftfreq(M, pixel): k/(M*pixel) for k < M/2, (k-M)/(M*pixel) otherwise
+    const double f = (double)(k < M / 2 ? k : k - M) / ((double)M * p.pixel_A);
+    const double ph = -M_PI * p.lambda_A * p.dz_A * f * f;
+    hs[k] = make_float2((float)(std::cos(ph) / M), (float)(std::sin(ph) / M));
+  }
+
+  // Workspace per position in flight (gradient mode).
+  const size_t MM = (size_t)M * M;
+  const size_t per_pos = (size_t)(2 * p.S - 1) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
+  const int64_t cap = p.workspace_bytes ? p.workspace_bytes : kDefaultWorkspace;
+  int64_t chunk = cap / (int64_t)per_pos;
+  if (chunk < 1) {
+    delete pl;
+    return fail(PTYCHO_ERR_NOMEM, "workspace_bytes too small for one position");
+  }
+  const int n = p.N > 0 ? p.N : 1;
+  if (chunk >= n) {
+    chunk = n;
+  } else {
+    const int blocks_per_wave = pl->sm_count * (M == 128 ? 1 : 4);
+    if (chunk > blocks_per_wave) chunk -= chunk % blocks_per_wave;
+  }
+  pl->chunk = (int)chunk;
+
+  rc = PTYCHO_OK;
+  if (!rc) rc = dev_alloc(&pl->d_tw, M, "twiddles");
+  if (!rc) rc = dev_alloc(&pl->d_hs, M, "propagator");
+  if (!rc) rc = dev_alloc(&pl->ws_psi, (size_t)pl->chunk * (p.S - 1) * MM, "wave workspace");
+  if (!rc) rc = dev_alloc(&pl->ws_gphi, (size_t)pl->chunk * p.S * MM, "adjoint workspace");
+  if (!rc) rc = dev_alloc(&pl->ws_gp, (size_t)pl->chunk * MM, "probe-gradient workspace");
+  if (!rc) rc = dev_alloc(&pl->gp_part, (size_t)kProbeSplit * MM, "probe-gradient partials");
+  if (!rc) rc = dev_alloc(&pl->loss_part, (size_t)pl->chunk, "loss partials");
+  if (!rc) rc = dev_alloc(&pl->d_scal, 8, "scalars");
+  if (!rc) rc = dev_alloc(&pl->norm_part, kNormParts, "norm partials");
+  if (!rc) rc = dev_alloc(&pl->d_status, 1, "status");
+  if (rc) {
+    free_plan(pl);
+    return rc;
+  }
+  if (cudaMallocHost(&pl->h_pos, sizeof(int32_t) * 2 * (size_t)n) != cudaSuccess ||
+      cudaMallocHost(&pl->h_scal, sizeof(double) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(pl);
+    return fail(PTYCHO_ERR_NOMEM, "pinned host allocation failed");
+  }
+  pl->ws_bytes = (int64_t)pl->chunk * (int64_t)per_pos;
+  if ((e = cudaMemcpy(pl->d_tw, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(pl->d_hs, hs.data(), M * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(pl->d_scal, 0, 8 * sizeof(double))) != cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "table upload");
+  }
+  *out = pl;
+  return PTYCHO_OK;
+}
+
+int ptycho_plan_destroy(ptycho_plan plan) {
+  g_last_error.clear();
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return PTYCHO_OK;
+}
+
+int ptycho_plan_info(ptycho_plan plan, int32_t* chunk_positions, int64_t* workspace_bytes) {
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  if (chunk_positions) *chunk_positions = plan->chunk;
+  if (workspace_bytes) *workspace_bytes = plan->ws_bytes;
+  return PTYCHO_OK;
+}
+
+int ptycho_plan_status(ptycho_plan plan) {
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  int h = 0;
+  CUDA_TRY(cudaMemcpy(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(plan->d_status, 0, sizeof(int)));
+  if (h) return fail(h, "a probe window outside the object was skipped on the device");
+  return PTYCHO_OK;
+}
+
+int ptycho_forward(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
+                   ptycho_c64* psi_out, float* intens_out, void* stream) {
+  g_last_error.clear();
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  if (!psi_out && !intens_out) return fail(PTYCHO_ERR_ARG, "psi_out and intens_out are both NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  if ((rc = check_array(probe, "probe", true)) || (rc = check_array(obj, "obj", true)) ||
+      (rc = check_array(psi_out, "psi_out", false)) || (rc = check_array(intens_out, "intens_out", false)))
+    return rc;
+  if ((rc = check_positions(plan, pos_yx, st))) return rc;
+  const ptycho_params& p = plan->p;
+  ChainArgs a = base_args(plan, pos_yx, probe, obj, nullptr);
+  a.psi_out = reinterpret_cast<float2*>(psi_out);
+  a.int_out = intens_out;
+  const int step = 1 << 20;
+  for (int c0 = 0; c0 < p.N; c0 += step) {
+    a.pos_begin = c0;
+    a.n_pos = p.N - c0 < step ? p.N - c0 : step;
+    CUDA_TRY(launch_chain(p.M, MODE_FORWARD, a, st));
+  }
+  return PTYCHO_OK;
+}
+
+int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
+                     const float* meas_I, double* loss_out, ptycho_c64* grad_obj, ptycho_c64* grad_probe,
+                     void* stream) {
+  g_last_error.clear();
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  if ((rc = check_array(probe, "probe", true)) || (rc = check_array(obj, "obj", true)) ||
+      (rc = check_array(meas_I, "meas_I", plan->p.N > 0)) || (rc = check_array(grad_obj, "grad_obj", false)) ||
+      (rc = check_array(grad_probe, "grad_probe", false)))
+    return rc;
+  if ((rc = check_positions(plan, pos_yx, st))) return rc;
+  rc = run_loss_grad(plan, pos_yx, probe, obj, meas_I, reinterpret_cast<float2*>(grad_obj),
+                     reinterpret_cast<float2*>(grad_probe), 0, nullptr, 0.f, nullptr, 0.f, st);
+  if (rc) return rc;
+  return deliver_loss(plan, 0, loss_out, st);
+}
+
+int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj, const float* meas_I,
+                double alpha_obj, double alpha_probe, int32_t line_search, double* loss_out, double* t_out,
+                void* stream) {
+  g_last_error.clear();
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  if (!std::isfinite(alpha_obj) || !std::isfinite(alpha_probe))
+    return fail(PTYCHO_ERR_ARG, "step sizes must be finite");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ptycho_params& p = plan->p;
+  int rc;
+  if ((rc = check_array(probe, "probe", true)) || (rc = check_array(obj, "obj", true)) ||
+      (rc = check_array(meas_I, "meas_I", p.N > 0)))
+    return rc;
+  if ((rc = check_positions(plan, pos_yx, st))) return rc;
+  const size_t nO = (size_t)p.S * p.H * p.W, nP = (size_t)p.M * p.M;
+  if (!plan->g_obj && (rc = dev_alloc(&plan->g_obj, nO, "step object gradient"))) return rc;
+  if (!plan->g_probe && (rc = dev_alloc(&plan->g_probe, nP, "step probe gradient"))) return rc;
+  rc = run_loss_grad(plan, pos_yx, probe, obj, meas_I, plan->g_obj, plan->g_probe, 0, nullptr, 0.f, nullptr, 0.f, st);
+  if (rc) return rc;
+  if ((rc = deliver_loss(plan, 0, loss_out, st))) return rc;
+  float2* O = reinterpret_cast<float2*>(obj);
+  float2* P = reinterpret_cast<float2*>(probe);
+  double t = 1.0;
+  if (line_search) {
+    CUDA_TRY(launch_norm2(plan->g_obj, nO, plan->norm_part, kNormParts, plan->d_scal, 1, st));
+    CUDA_TRY(launch_norm2(plan->g_probe, nP, plan->norm_part, kNormParts, plan->d_scal, 2, st));
+    CUDA_TRY(cudaMemcpyAsync(plan->h_scal, plan->d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const double F0 = plan->h_scal[0];
+    const double dec = alpha_obj * plan->h_scal[1] + alpha_probe * plan->h_scal[2];
+    bool accepted = false;
+    for (int k = 0; k <= 20; ++k) {
+      rc = run_loss_grad(plan, pos_yx, probe, obj, meas_I, nullptr, nullptr, 3, plan->g_obj,
+                         (float)(-t * alpha_obj), plan->g_probe, (float)(-t * alpha_probe), st);
+      if (rc) return rc;
+      CUDA_TRY(cudaMemcpyAsync(plan->h_scal + 3, plan->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      if (plan->h_scal[3] <= F0 - 1e-4 * t * dec) {
+        accepted = true;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!accepted) t = 0.0;
+  }
+  if (t > 0.0) {
+    CUDA_TRY(launch_axpy(O, plan->g_obj, O, -t * alpha_obj, nO, st));
+    CUDA_TRY(launch_axpy(P, plan->g_probe, P, -t * alpha_probe, nP, st));
+  }
+  if (t_out) *t_out = t;
+  return PTYCHO_OK;
+}
+
+}  // extern "C"

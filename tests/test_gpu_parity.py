@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Bar (FP32 path): relative L2 error <= 1e-5 on the loss and both gradients.
+Where the oracle's loss is 0 (noise-free data at the true object) the check is
+absolute: F_gpu <= 1e-6 * sum(I).
+"""
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from paper_2205_06327_gb300 import synth
+from tests.helpers import TOL_FP32, measurements, propagator, rel_l2, start_object, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda", 0)
+
+
+def _plan(wl, dev, **kw):
+    from paper_2205_06327_gb300 import api
+    return api.Plan(api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A), dev, **kw)
+
+
+def _run(wl, obj, I, dev, probe=None, **kw):
+    plan = _plan(wl, dev, **kw)
+    probe = wl.probe if probe is None else probe
+    loss, gO, gP = plan.loss_grad(to_dev(wl.pos, torch.int32, dev), to_dev(probe, torch.complex64, dev),
+                                  to_dev(obj, torch.complex64, dev), to_dev(I, torch.float32, dev))
+    torch.cuda.synchronize()
+    out = loss.item(), gO.cpu().numpy(), gP.cpu().numpy()
+    plan.close()
+    return out
+
+
+def _check(wl, obj, I, dev, tol=TOL_FP32, **kw):
+    h = propagator(wl)
+    L, gO, gP = orc.loss_grad(wl.probe, obj, wl.pos, I.astype(np.float64), h)
+    l, go, gp = _run(wl, obj, I, dev, **kw)
+    el = abs(l - L) / abs(L)
+    eo, ep = rel_l2(go, gO), rel_l2(gp, gP)
+    print(f"{wl.name}: loss {el:.2e} gO {eo:.2e} gP {ep:.2e}")
+    assert el <= tol and eo <= tol and ep <= tol, (el, eo, ep)
+    return l, go, gp
+
+
+# --------------------------------------------------------------- workloads
+
+def test_single_slice_workload_vacuum_start(dev):
+    wl = synth.workload_single_slice()
+    I = measurements(wl)
+    _check(wl, start_object(wl, "vacuum"), I, dev)
+
+
+def test_single_slice_workload_at_truth_is_zero(dev):
+    wl = synth.workload_single_slice()
+    I = measurements(wl)
+    l, go, gp = _run(wl, wl.obj, I, dev)
+    assert l <= 1e-6 * float(I.sum())
+    _, gO_ref, _ = orc.loss_grad(wl.probe, start_object(wl, "vacuum"), wl.pos, I.astype(np.float64), propagator(wl))
+    assert np.linalg.norm(go) <= 1e-3 * np.linalg.norm(gO_ref)
+
+
+def test_multislice_workload_full_size(dev):
+    """All 576 positions, 16 slices of 384^2, Poisson data, perturbed start."""
+    wl = synth.workload_multislice()
+    I = measurements(wl, counts_seed=1002)
+    _check(wl, start_object(wl, "perturbed", 2), I, dev)
+
+
+def test_multislice_workload_at_truth_with_noise(dev):
+    wl = synth.workload_multislice()
+    wl.pos = wl.pos[::7]
+    I = measurements(wl, counts_seed=1002)
+    _check(wl, wl.obj, I, dev)
+
+
+@pytest.mark.parametrize("M,S,ny,nx,step", [(64, 1, 3, 5, 7), (64, 5, 4, 3, 11), (128, 2, 2, 3, 20),
+                                             (128, 7, 3, 3, 13)])
+def test_random_problems_nonunimodular(dev, M, S, ny, nx, step):
+    wl = synth.workload_random(M, S, ny, nx, step, seed=M + S, amp_jitter=0.2)
+    I = (measurements(wl) * 1.2).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 5), I, dev)
+
+
+def test_perovskite_subset(dev):
+    """PbTiO3-shaped object (30 x 640x656) with a 6x7 block of the 4-px raster."""
+    wl = synth.workload_perovskite(n_rows=6, n_cols=7)
+    wl.pos = wl.pos + np.array([200, 240], np.int32)
+    I = measurements(wl, counts_seed=1003)
+    _check(wl, start_object(wl, "perturbed", 3), I, dev)
+
+
+# ------------------------------------------------------------------ forward
+
+def test_forward_far_field_and_intensity(dev):
+    from paper_2205_06327_gb300 import api
+    wl = synth.workload_random(128, 3, 2, 2, 17, seed=3, amp_jitter=0.1)
+    Psi = orc.forward(wl.probe, wl.obj, wl.pos, propagator(wl))
+    plan = _plan(wl, dev)
+    psi, inten = plan.forward(to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+                              to_dev(wl.obj, torch.complex64, dev), want_psi=True, want_intensity=True)
+    torch.cuda.synchronize()
+    assert rel_l2(psi.cpu().numpy(), Psi) <= TOL_FP32
+    assert rel_l2(inten.cpu().numpy(), np.abs(Psi) ** 2) <= TOL_FP32
+
+
+# ------------------------------------------------------- structure and edges
+
+def test_deterministic_bitwise(dev):
+    wl = synth.workload_random(64, 4, 4, 4, 6, seed=11)
+    I = (measurements(wl) * 0.8).astype(np.float32)
+    obj = start_object(wl, "perturbed", 1)
+    a = _run(wl, obj, I, dev)
+    b = _run(wl, obj, I, dev)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_tiling_and_chunking_invariance(dev):
+    """Eq. 2 / Sec. III: tile shape does not change the per-pixel summation order
+    (bit-identical); chunking the positions only reassociates the sum."""
+    wl = synth.workload_random(64, 3, 6, 5, 5, seed=12)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    obj = start_object(wl, "perturbed", 2)
+    ref = _run(wl, obj, I, dev)
+    tiled = _run(wl, obj, I, dev, tile=((wl.H + 7) // 8, (wl.W + 7) // 8))
+    assert np.array_equal(ref[1], tiled[1])
+    per_pos = (2 * wl.S - 1) * wl.M * wl.M * 8 + wl.M * wl.M * 8 + 8
+    chunked = _run(wl, obj, I, dev, workspace_bytes=7 * per_pos)
+    assert abs(chunked[0] - ref[0]) <= 1e-12 * abs(ref[0])
+    assert rel_l2(chunked[1], ref[1]) <= 1e-6 and rel_l2(chunked[2], ref[2]) <= 1e-6
+
+
+def test_window_at_object_corners(dev):
+    wl = synth.workload_random(64, 2, 1, 1, 1, seed=13, amp_jitter=0.1)
+    wl.pos = np.array([[0, 0], [wl.H - 64, wl.W - 64], [0, wl.W - 64], [wl.H - 64, 0]], np.int32)
+    I = (measurements(wl) * 0.7).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 4), I, dev)
+
+
+def test_zero_positions(dev):
+    wl = synth.workload_random(64, 2, 1, 1, 1, seed=14)
+    wl.pos = np.zeros((0, 2), np.int32)
+    I = np.zeros((0, 64, 64), np.float32)
+    l, go, gp = _run(wl, wl.obj, I, dev)
+    assert l == 0.0 and not go.any() and not gp.any()
+
+
+def test_errors_are_reported_not_faulted(dev):
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300._lib import PTYCHO_ERR_POSITION, PTYCHO_ERR_UNSUPPORTED, PtychoError
+    wl = synth.workload_random(64, 2, 2, 2, 5, seed=15)
+    I = measurements(wl)
+    bad = wl.pos.copy()
+    bad[1] = [wl.H - 63, 0]
+    plan = _plan(wl, dev)
+    args = (to_dev(bad, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+            to_dev(wl.obj, torch.complex64, dev), to_dev(I, torch.float32, dev))
+    with pytest.raises(PtychoError) as e:
+        plan.loss_grad(*args)
+    assert e.value.code == PTYCHO_ERR_POSITION
+    # asynchronous check: the device skips the window and reports it afterwards
+    aplan = _plan(wl, dev, async_check=True)
+    aplan.loss_grad(*args)
+    torch.cuda.synchronize()
+    with pytest.raises(PtychoError) as e:
+        aplan.status()
+    assert e.value.code == PTYCHO_ERR_POSITION
+    aplan.status()  # cleared
+    with pytest.raises(PtychoError) as e:
+        api.Plan(api.Geometry(100, 2, 200, 200, 4), dev)
+    assert e.value.code == PTYCHO_ERR_UNSUPPORTED
+    # the context is still usable
+    _check(wl, wl.obj * 0.9, I, dev)
+
+
+# --------------------------------------------------------- gradient checks
+
+def test_gpu_gradient_matches_fp64_finite_differences(dev):
+    """Directional derivatives of the FP64 loss (central differences) against
+    Re<g_gpu, d> on the multislice workload (a block of 36 positions)."""
+    wl = synth.workload_multislice()
+    wl.pos = wl.pos.reshape(24, 24, 2)[8:14, 8:14].reshape(-1, 2).copy()
+    I = measurements(wl, counts_seed=1002)
+    obj = start_object(wl, "perturbed", 6)
+    _, go, gp = _run(wl, obj, I, dev)
+    h = propagator(wl)
+    g = synth.rng(8)
+    eps = 1e-6
+    for _ in range(3):
+        dO = g.standard_normal(obj.shape) + 1j * g.standard_normal(obj.shape)
+        dP = g.standard_normal(wl.probe.shape) + 1j * g.standard_normal(wl.probe.shape)
+        fd = (orc.loss(wl.probe + eps * dP, obj + eps * dO, wl.pos, I.astype(np.float64), h)
+              - orc.loss(wl.probe - eps * dP, obj - eps * dO, wl.pos, I.astype(np.float64), h)) / (2 * eps)
+        an = np.real(np.vdot(go.astype(np.complex128), dO) + np.vdot(gp.astype(np.complex128), dP))
+        assert abs(an - fd) <= 1e-5 * abs(fd), (an, fd)
+
+
+def test_step_fixed_and_line_search(dev):
+    from paper_2205_06327_gb300 import api
+    wl = synth.workload_random(64, 3, 3, 3, 8, seed=16, amp_jitter=0.1)
+    I = measurements(wl)
+    obj = start_object(wl, "perturbed", 7)
+    h = propagator(wl)
+    plan = _plan(wl, dev)
+    pos = to_dev(wl.pos, torch.int32, dev)
+    Id = to_dev(I, torch.float32, dev)
+    P = to_dev(wl.probe, torch.complex64, dev)
+    O = to_dev(obj, torch.complex64, dev)
+    a_o, a_p = 1e-3, 1e-5
+    loss, t = plan.step(pos, P, O, Id, a_o, a_p)
+    Pn, On, F0, _ = orc.step(wl.probe.astype(np.complex64).astype(np.complex128),
+                             obj.astype(np.complex64).astype(np.complex128), wl.pos, I.astype(np.float64), h, a_o, a_p)
+    assert t == 1.0 and abs(loss.item() - F0) <= 1e-5 * F0
+    assert rel_l2(O.cpu().numpy(), On) <= 1e-6 and rel_l2(P.cpu().numpy(), Pn) <= 1e-6
+    # Armijo with a deliberately large step backtracks and decreases the loss
+    L0 = plan.loss_grad(pos, P, O, Id)[0].item()
+    loss, t = plan.step(pos, P, O, Id, 50.0, 0.5, line_search=True)
+    L1 = plan.loss_grad(pos, P, O, Id)[0].item()
+    assert 0.0 < t < 1.0 and L1 < L0
+
+
+def test_autograd_function(dev):
+    from paper_2205_06327_gb300.autograd import ptycho_loss
+    wl = synth.workload_random(64, 2, 2, 3, 9, seed=17)
+    I = measurements(wl)
+    obj0 = start_object(wl, "perturbed", 8)
+    plan = _plan(wl, dev)
+    O = to_dev(obj0, torch.complex64, dev).requires_grad_(True)
+    P = to_dev(wl.probe, torch.complex64, dev).requires_grad_(True)
+    L = ptycho_loss(O, P, plan, to_dev(wl.pos, torch.int32, dev), to_dev(I, torch.float32, dev))
+    (2.0 * L).backward()
+    Lr, gO, gP = orc.loss_grad(wl.probe, obj0, wl.pos, I.astype(np.float64), propagator(wl))
+    assert abs(L.item() - Lr) <= 1e-5 * Lr
+    assert rel_l2(O.grad.cpu().numpy(), 2 * gO) <= TOL_FP32
+    assert rel_l2(P.grad.cpu().numpy(), 2 * gP) <= TOL_FP32
