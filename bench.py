@@ -1,0 +1,456 @@
+"""Throughput of the multislice loss + object/probe gradient on GB300.
+
+One step = one full evaluation of the hot path through the C-ABI
+(``ptycho_loss_grad``): the slice chain of every position (forward model,
+amplitude residual, exact adjoint), the tiled object-gradient accumulation,
+the probe-gradient and FP64 loss reductions.  Metric: probe positions per
+second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1|2|3] [--impl reference]
+
+Inputs are synthetic (seeded) and resident in HBM when the timed region
+starts; the L2 is flushed (512 MiB write) between timed steps, outside the
+per-step CUDA events.  ``e2e`` repeats the measurement through the public
+Python API with host (pinned) inputs and host results, copies included.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the path has no data exchange between GPUs in this build); rank 0
+prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "probe-positions/s for loss+object/probe gradient; % of HBM/tensor roofline"
+UNIT = "positions/s"
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+
+def workload_for(config_id: int):
+    from paper_2205_06327_gb300 import synth
+    return synth.workload(config_id)
+
+
+def start_object(wl, seed: int = 7):
+    """A reconstruction iterate near the truth (seeded perturbation)."""
+    from paper_2205_06327_gb300 import synth
+    g = synth.rng(seed)
+    return wl.obj * np.exp(0.1j * g.standard_normal(wl.obj.shape))
+
+
+def flops_per_position(M: int, S: int) -> float:
+    """Algorithmic FP32 flops of one position's chain + gradient patch.
+
+    FFTs: (2S-1) forward + (2S-1) adjoint 2-D transforms at 5 M^2 log2(M^2)
+    each.  Elementwise (per pixel): S transmissions and S-1 propagator
+    multiplies forward, the same adjoint (6 flops per complex multiply), the
+    residual (10) and the object-gradient patch conj(psi) g (8 with the add).
+    """
+    fft = 5.0 * M * M * math.log2(M * M)
+    n_fft = 4 * S - 2
+    elem = M * M * (6 * S + 6 * (S - 1) + 10 + 6 * S + 6 * (S - 1) + 8 * S)
+    return n_fft * fft + elem
+
+
+def chain_flops_per_position(M: int, S: int) -> float:
+    """Flops of the slice-chain kernel alone (everything but the patch products)."""
+    return flops_per_position(M, S) - 8.0 * S * M * M
+
+
+def hbm_bytes_per_evaluation(wl) -> float:
+    """Minimum bytes the method moves per evaluation: intensities once, object
+    once, object gradient once, probe and its gradient."""
+    return (wl.N * wl.M * wl.M * 4 + 2 * wl.S * wl.H * wl.W * 8 + 2 * wl.M * wl.M * 8)
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): process pool, spawn context
+# --------------------------------------------------------------------------
+
+_ORC_STATE = {}
+
+
+def _oracle_init(config_id: int):
+    from oracle import ptycho_oracle as orc
+    wl = workload_for(config_id)
+    _ORC_STATE["wl"] = wl
+    _ORC_STATE["obj"] = start_object(wl)
+    _ORC_STATE["h"] = orc.fresnel_propagator(wl.M, wl.lambda_A, wl.dz_A, wl.pixel_A)
+
+
+def _oracle_task(args):
+    from oracle import ptycho_oracle as orc
+    idx, I = args
+    wl = _ORC_STATE["wl"]
+    L, gO, gP = orc.loss_grad(wl.probe, _ORC_STATE["obj"], wl.pos[idx], I.astype(np.float64), _ORC_STATE["h"])
+    # return only the bounding box of the windows touched
+    y0, x0 = wl.pos[idx].min(0)
+    y1, x1 = wl.pos[idx].max(0) + wl.M
+    return L, (int(y0), int(x0)), gO[:, y0:y1, x0:x1], gP
+
+
+class OraclePool:
+    def __init__(self, config_id: int, cores: int):
+        self.cores = cores
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(config_id,))
+        self.pool.map(abs, range(cores))  # wait for the workers
+
+    def evaluate(self, wl, idx: np.ndarray, I: np.ndarray) -> float:
+        """One oracle loss+gradient over positions idx (I rows for them); returns wall seconds."""
+        parts = np.array_split(np.asarray(idx), min(self.cores, len(idx)))
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_task, [(p, I[p]) for p in parts if len(p)])
+        L = 0.0
+        gO = np.zeros((wl.S, wl.H, wl.W), complex)
+        gP = np.zeros((wl.M, wl.M), complex)
+        for l, (y0, x0), g, p in res:
+            L += l
+            gO[:, y0:y0 + g.shape[1], x0:x0 + g.shape[2]] += g
+            gP += p
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_sample_indices(wl, n_sample: int) -> np.ndarray:
+    if n_sample >= wl.N:
+        return np.arange(wl.N)
+    return np.linspace(0, wl.N - 1, n_sample).round().astype(np.int64)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str | None):
+        self.path = path
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+            if self.path:
+                with open(self.path, "w") as f:
+                    f.write(self.FIELDS + "\n" + "\n".join(self.lines) + "\n")
+        return False
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (replicas; host logic covered by gloo tests)
+# --------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# arms
+# --------------------------------------------------------------------------
+
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def run_reference(args, world, rank):
+    """FP64 CPU oracle on the host cores: each step one bounded sample."""
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    wl = workload_for(args.config)
+    pool = OraclePool(args.config, cores)
+    # measured intensities for the sample from the oracle itself (noise-free, scaled)
+    from oracle import ptycho_oracle as orc
+    idx = cpu_sample_indices(wl, args.cpu_sample)
+    h = orc.fresnel_propagator(wl.M, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    I = np.zeros((wl.N, wl.M, wl.M), np.float32)
+    I[idx] = orc.intensities(wl.probe, wl.obj, wl.pos[idx], h).astype(np.float32)
+    for _ in range(args.warmup):
+        pool.evaluate(wl, idx, I)
+    times = [pool.evaluate(wl, idx, I) for _ in range(args.steps)]
+    pool.close()
+    t = float(np.mean(times))
+    v = len(idx) / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "positions_per_step": int(len(idx)), "M": wl.M, "S": wl.S,
+                   "object": [wl.H, wl.W]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(idx)} of {wl.N} positions per step (loss + object/probe gradient)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, world, rank, local, pool):
+    import torch
+
+    from paper_2205_06327_gb300 import api
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    wl = workload_for(args.config)
+    if args.positions:
+        wl.pos = wl.pos[: args.positions]
+    obj0 = start_object(wl)
+    geom = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    tile = (0, 0)
+    if args.config == 3:
+        tile = ((wl.H + 7) // 8, (wl.W + 7) // 8)  # 8 x 8 tessellation of the gradient
+    plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile)
+    pos = torch.from_numpy(wl.pos).to(device)
+    probe = torch.from_numpy(wl.probe.astype(np.complex64)).to(device)
+    obj_true = torch.from_numpy(wl.obj.astype(np.complex64)).to(device)
+    obj = torch.from_numpy(obj0.astype(np.complex64)).to(device)
+    # measurements: forward model at the truth (GPU), Poisson counts (seeded)
+    _, I = plan.forward(pos, probe, obj_true, want_psi=False, want_intensity=True)
+    del obj_true
+    if wl.counts is not None:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(1000 + args.config)
+        I = torch.poisson(I, generator=gen)
+    gO = torch.empty((wl.S, wl.H, wl.W), dtype=torch.complex64, device=device)
+    gP = torch.empty((wl.M, wl.M), dtype=torch.complex64, device=device)
+    loss = torch.empty((), dtype=torch.float64, device=device)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+    lib, h, sh = plan.lib, plan._h, stream.cuda_stream
+
+    def step():
+        rc = lib.ptycho_loss_grad(h, pos.data_ptr(), probe.data_ptr(), obj.data_ptr(), I.data_ptr(),
+                                  loss.data_ptr(), gO.data_ptr(), gP.data_ptr(), sh)
+        if rc:
+            from paper_2205_06327_gb300._lib import check
+            check(rc)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(device)
+    plan.timing(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    wall0 = time.perf_counter()
+    with clocks:
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(device)
+    wall = time.perf_counter() - wall0
+    barrier(world, device)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tm = plan.timing(reset=True)
+    plan.status()
+    t_step = float(np.mean(step_ms)) / 1e3
+    t_max = reduce_max(t_step, world, device)
+    value = world * wl.N / t_max
+
+    # roofline of the dominant kernel (slice chain): FP32 ALU bound
+    chain_ms = tm["chain_ms"] / max(tm["chain_launches"], 1)
+    chain_pos = tm["chain_positions"] / max(tm["chain_launches"], 1)
+    chain_flops = chain_flops_per_position(wl.M, wl.S) * chain_pos
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = chain_flops / (chain_ms / 1e3) / 1e12
+    pk = peaks()
+    accum_ms = tm["accum_ms"] / max(tm["accum_launches"], 1)
+    accum_bytes = 2.0 * wl.N * wl.S * wl.M * wl.M * 8 + wl.S * wl.H * wl.W * 8
+    launches_per_step = tm["launches"] / args.steps
+
+    # end to end through the public API: pinned host inputs, host results
+    e2e = None
+    if not args.no_e2e:
+        hp = {k: v.cpu().pin_memory() for k, v in (("pos", pos), ("probe", probe), ("obj", obj), ("I", I))}
+        h2d = sum(v.numel() * v.element_size() for v in hp.values())
+        d2h = 8 + gO.numel() * 8 + gP.numel() * 8
+        eplan = api.Plan(geom, device, async_check=True, tile=tile)
+        for _ in range(2):
+            eplan.loss_grad(hp["pos"], hp["probe"], hp["obj"], hp["I"])
+        torch.cuda.synchronize(device)
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(3)
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            L, go, gp = eplan.loss_grad(hp["pos"], hp["probe"], hp["obj"], hp["I"])
+            _ = float(L)
+            ts.append(time.perf_counter() - t0)
+        eplan.close()
+        te = reduce_max(float(np.mean(ts)), world, device)
+        e2e = {"value": world * wl.N / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if pool is not None and rank == 0:
+        idx = cpu_sample_indices(wl, args.cpu_sample)
+        I_host = I.cpu().numpy()
+        pool.evaluate(wl, idx[: min(len(idx), pool.cores)], I_host)  # warm the workers
+        t_cpu = pool.evaluate(wl, idx, I_host)
+        cpu = {"value": len(idx) / t_cpu, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+               "sample": f"{len(idx)} of {wl.N} positions, one loss + object/probe gradient evaluation "
+                         f"(FP64 NumPy, process pool)"}
+
+    csum = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "positions": wl.N, "M": wl.M, "S": wl.S, "object": [wl.H, wl.W],
+                   "tiles": list(tile) if tile != (0, 0) else [64, 64],
+                   "l2": "flushed between timed steps (512 MiB write, outside the step events)",
+                   "replicas": world, "wall_s": wall},
+        "roofline": {"bound": "alu", "kernel": "k_chain (slice chain, gradient mode)",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "kernel_ms": chain_ms, "kernel_share": tm["chain_ms"] / max(sum(step_ms), 1e-9)},
+        "hbm_kernels": {"accum_obj_grad": {"ms": accum_ms, "bytes": accum_bytes,
+                                           "gbs": accum_bytes / (accum_ms / 1e3) / 1e9 if accum_ms else None,
+                                           "frac": (accum_bytes / (accum_ms / 1e3) / 1e9) / pk["hbm_gbs"]
+                                           if accum_ms else None, "peak_src": pk["src"]}},
+        "path_bound_ms": max(flops_per_position(wl.M, wl.S) * wl.N / (peak_tflops * 1e12),
+                             hbm_bytes_per_evaluation(wl) / (pk["hbm_gbs"] * 1e9)) * 1e3,
+        "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(round(launches_per_step * args.steps)),
+        "gpu_launches_per_step": launches_per_step,
+        "clocks": {"sm_mhz": csum["sm_mhz"], "sm_max_mhz": csum["sm_max_mhz"], "reasons": csum["reasons"]},
+    }
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=576)
+    ap.add_argument("--positions", type=int, default=0, help="first N positions only (profiling cases)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # spawn the oracle's workers before the first CUDA call
+        pool = OraclePool(args.config, os.cpu_count() or 1)
+    try:
+        return run_gpu(args, world, rank, local, pool)
+    finally:
+        if pool is not None:
+            pool.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -66,6 +66,9 @@ extern "C" {
                                       on the host; out-of-range windows are
                                       skipped on the device and reported by
                                       ptycho_plan_status() */
+#define PTYCHO_FLAG_TIMING      2  /* record CUDA events around every kernel
+                                      family on the call's stream; read them
+                                      with ptycho_plan_timing() */
 
 typedef struct {
   float re, im;
@@ -144,6 +147,23 @@ PTYCHO_API int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const p
 PTYCHO_API int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj,
                 const float* meas_I, double alpha_obj, double alpha_probe,
                 int32_t line_search, double* loss_out, double* t_out, void* stream);
+
+/* Per-kernel-family device time and launch counts accumulated since the
+ * last reset.  Times are filled only for plans created with
+ * PTYCHO_FLAG_TIMING (CUDA events on the call's stream); launch counts are
+ * always kept.  Synchronises on the recorded events.  reset != 0 clears. */
+typedef struct {
+  double chain_ms;        /* per-position slice-chain kernels (forward/adjoint) */
+  double accum_ms;        /* object-gradient tiled accumulation */
+  double probe_ms;        /* probe-gradient reduction */
+  double other_ms;        /* loss reduction, checks, step vector kernels */
+  int64_t chain_launches;
+  int64_t accum_launches;
+  int64_t launches;       /* all kernels this library launched */
+  int64_t chain_positions; /* positions processed by the chain kernels */
+} ptycho_timing;
+
+PTYCHO_API int ptycho_plan_timing(ptycho_plan plan, ptycho_timing* out, int32_t reset);
 
 /* Text of the last error on the calling host thread ("" if none). */
 PTYCHO_API const char* ptycho_last_error(void);

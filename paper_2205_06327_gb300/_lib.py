@@ -21,6 +21,7 @@ PTYCHO_ERR_TIMEOUT = -5
 PTYCHO_ERR_UNSUPPORTED = -6
 PTYCHO_FP32 = 0
 PTYCHO_FLAG_ASYNC_CHECK = 1
+PTYCHO_FLAG_TIMING = 2
 
 ERROR_NAMES = {
     PTYCHO_ERR_ARG: "PTYCHO_ERR_ARG",
@@ -34,7 +35,8 @@ ERROR_NAMES = {
 # Every symbol include/ptycho.h declares.
 EXPORTED = [
     "ptycho_plan_create", "ptycho_plan_destroy", "ptycho_plan_info", "ptycho_plan_status",
-    "ptycho_forward", "ptycho_loss_grad", "ptycho_step", "ptycho_last_error", "ptycho_version",
+    "ptycho_forward", "ptycho_loss_grad", "ptycho_step", "ptycho_plan_timing", "ptycho_last_error",
+    "ptycho_version",
 ]
 
 
@@ -46,6 +48,17 @@ class PtychoParams(C.Structure):
         ("workspace_bytes", C.c_int64),
         ("tile_h", C.c_int32), ("tile_w", C.c_int32),
     ]
+
+
+class PtychoTiming(C.Structure):
+    _fields_ = [
+        ("chain_ms", C.c_double), ("accum_ms", C.c_double), ("probe_ms", C.c_double), ("other_ms", C.c_double),
+        ("chain_launches", C.c_int64), ("accum_launches", C.c_int64), ("launches", C.c_int64),
+        ("chain_positions", C.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class PtychoError(RuntimeError):
@@ -75,6 +88,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ptycho_forward": ([vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_loss_grad": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_step": ([vp, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp], C.c_int),
+        "ptycho_plan_timing": ([vp, C.POINTER(PtychoTiming), i32], C.c_int),
         "ptycho_last_error": ([], C.c_char_p),
         "ptycho_version": ([], C.c_char_p),
     }

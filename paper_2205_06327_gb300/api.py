@@ -46,7 +46,8 @@ class Plan:
     """A ``ptycho_plan``: tables and workspace for one problem shape."""
 
     def __init__(self, geom: Geometry, device: torch.device | int | str = "cuda",
-                 workspace_bytes: int = 0, tile: tuple[int, int] = (0, 0), async_check: bool = False):
+                 workspace_bytes: int = 0, tile: tuple[int, int] = (0, 0), async_check: bool = False,
+                 timing: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("libptycho needs a CUDA device; there is no CPU fallback")
         self.lib = _lib.load()
@@ -58,7 +59,7 @@ class Plan:
         p.M, p.S, p.H, p.W, p.N = geom.M, geom.S, geom.H, geom.W, geom.N
         p.lambda_A, p.dz_A, p.pixel_A = geom.lambda_A, geom.dz_A, geom.pixel_A
         p.precision = _lib.PTYCHO_FP32
-        p.flags = _lib.PTYCHO_FLAG_ASYNC_CHECK if async_check else 0
+        p.flags = (_lib.PTYCHO_FLAG_ASYNC_CHECK if async_check else 0) | (_lib.PTYCHO_FLAG_TIMING if timing else 0)
         p.workspace_bytes = int(workspace_bytes)
         p.tile_h, p.tile_w = int(tile[0]), int(tile[1])
         self._params = p
@@ -79,6 +80,13 @@ class Plan:
         c, w = C.c_int32(), C.c_int64()
         check(self.lib.ptycho_plan_info(self._h, C.byref(c), C.byref(w)))
         return w.value
+
+    def timing(self, reset: bool = True) -> dict:
+        """Per-kernel-family device milliseconds and launch counts since the last reset."""
+        t = _lib.PtychoTiming()
+        with torch.cuda.device(self.device):
+            check(self.lib.ptycho_plan_timing(self._h, C.byref(t), int(reset)))
+        return t.as_dict()
 
     def status(self) -> None:
         with torch.cuda.device(self.device):

@@ -72,12 +72,24 @@ struct ptycho_plan_s {
   // gradient-descent step buffers (allocated on first use)
   float2* g_obj = nullptr;
   float2* g_probe = nullptr;
+  // kernel timing: event pairs per kernel family, launch counters
+  struct Mark {
+    int kind;
+    cudaEvent_t start, stop;
+  };
+  std::vector<Mark> marks;
+  size_t n_marks = 0;
+  ptycho_timing tm{};
 };
 
 namespace {
 
 void free_plan(ptycho_plan pl) {
   if (!pl) return;
+  for (auto& m : pl->marks) {
+    cudaEventDestroy(m.start);
+    cudaEventDestroy(m.stop);
+  }
   cudaFree(pl->d_tw);
   cudaFree(pl->d_hs);
   cudaFree(pl->ws_psi);
@@ -154,6 +166,39 @@ int check_array(const void* ptr, const char* name, bool required) {
   return PTYCHO_OK;
 }
 
+enum Kind { K_CHAIN = 0, K_ACCUM = 1, K_PROBE = 2, K_OTHER = 3 };
+
+// Run `launch` (which enqueues `n_kernels` kernels on st) between two CUDA
+// events when the plan records timings; always count the launches.
+template <class F>
+int timed(ptycho_plan pl, int kind, int n_kernels, cudaStream_t st, F&& launch) {
+  const bool rec = (pl->p.flags & PTYCHO_FLAG_TIMING) != 0;
+  ptycho_plan_s::Mark* m = nullptr;
+  if (rec) {
+    if (pl->n_marks == pl->marks.size()) {
+      ptycho_plan_s::Mark nm{kind, nullptr, nullptr};
+      CUDA_TRY(cudaEventCreate(&nm.start));
+      CUDA_TRY(cudaEventCreate(&nm.stop));
+      pl->marks.push_back(nm);
+    }
+    m = &pl->marks[pl->n_marks++];
+    m->kind = kind;
+    CUDA_TRY(cudaEventRecord(m->start, st));
+  }
+  CUDA_TRY(launch());
+  if (rec) CUDA_TRY(cudaEventRecord(m->stop, st));
+  pl->tm.launches += n_kernels;
+  if (kind == K_CHAIN) pl->tm.chain_launches += n_kernels;
+  if (kind == K_ACCUM) pl->tm.accum_launches += n_kernels;
+  return PTYCHO_OK;
+}
+
+#define TIMED(kind, nk, expr)                                            \
+  do {                                                                   \
+    int rc_ = timed(pl, kind, nk, st, [&]() -> cudaError_t { return expr; }); \
+    if (rc_) return rc_;                                                 \
+  } while (0)
+
 ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, const ptycho_c64* obj,
                     const float* meas) {
   ChainArgs a{};
@@ -196,7 +241,8 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     const int n = p.N - c0 < pl->chunk ? p.N - c0 : pl->chunk;
     a.pos_begin = c0;
     a.n_pos = n;
-    CUDA_TRY(launch_chain(p.M, want_grad ? MODE_GRAD : MODE_LOSS, a, st));
+    TIMED(K_CHAIN, 1, launch_chain(p.M, want_grad ? MODE_GRAD : MODE_LOSS, a, st));
+    pl->tm.chain_positions += n;
     if (grad_obj) {
       AccumArgs g{};
       g.pos = a.pos;
@@ -213,11 +259,11 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
       g.ws_gphi = pl->ws_gphi;
       g.grad_obj = grad_obj;
       g.accumulate = ci > 0;
-      CUDA_TRY(launch_accum_obj_grad(g, st));
+      TIMED(K_ACCUM, 1, launch_accum_obj_grad(g, st));
     }
     if (grad_probe)
-      CUDA_TRY(launch_probe_grad(pl->ws_gp, n, p.M, pl->gp_part, kProbeSplit, grad_probe, ci > 0, st));
-    CUDA_TRY(launch_loss_accum(pl->loss_part, n, pl->d_scal + slot, ci > 0, st));
+      TIMED(K_PROBE, 2, launch_probe_grad(pl->ws_gp, n, p.M, pl->gp_part, kProbeSplit, grad_probe, ci > 0, st));
+    TIMED(K_OTHER, 1, launch_loss_accum(pl->loss_part, n, pl->d_scal + slot, ci > 0, st));
   }
   return PTYCHO_OK;
 }
@@ -351,6 +397,28 @@ int ptycho_plan_status(ptycho_plan plan) {
   return PTYCHO_OK;
 }
 
+int ptycho_plan_timing(ptycho_plan plan, ptycho_timing* out, int32_t reset) {
+  g_last_error.clear();
+  if (!plan || !out) return fail(PTYCHO_ERR_ARG, "plan and out must be non-NULL");
+  ptycho_timing t = plan->tm;
+  t.chain_ms = t.accum_ms = t.probe_ms = t.other_ms = 0.0;
+  for (size_t i = 0; i < plan->n_marks; ++i) {
+    const auto& m = plan->marks[i];
+    CUDA_TRY(cudaEventSynchronize(m.stop));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, m.start, m.stop));
+    double* dst = m.kind == K_CHAIN ? &t.chain_ms : m.kind == K_ACCUM ? &t.accum_ms
+                : m.kind == K_PROBE ? &t.probe_ms : &t.other_ms;
+    *dst += ms;
+  }
+  *out = t;
+  if (reset) {
+    plan->tm = ptycho_timing{};
+    plan->n_marks = 0;
+  }
+  return PTYCHO_OK;
+}
+
 int ptycho_forward(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
                    ptycho_c64* psi_out, float* intens_out, void* stream) {
   g_last_error.clear();
@@ -367,10 +435,12 @@ int ptycho_forward(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* pr
   a.psi_out = reinterpret_cast<float2*>(psi_out);
   a.int_out = intens_out;
   const int step = 1 << 20;
+  ptycho_plan pl = plan;
   for (int c0 = 0; c0 < p.N; c0 += step) {
     a.pos_begin = c0;
     a.n_pos = p.N - c0 < step ? p.N - c0 : step;
-    CUDA_TRY(launch_chain(p.M, MODE_FORWARD, a, st));
+    TIMED(K_CHAIN, 1, launch_chain(p.M, MODE_FORWARD, a, st));
+    pl->tm.chain_positions += a.n_pos;
   }
   return PTYCHO_OK;
 }
@@ -415,10 +485,11 @@ int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptyc
   if ((rc = deliver_loss(plan, 0, loss_out, st))) return rc;
   float2* O = reinterpret_cast<float2*>(obj);
   float2* P = reinterpret_cast<float2*>(probe);
+  ptycho_plan pl = plan;
   double t = 1.0;
   if (line_search) {
-    CUDA_TRY(launch_norm2(plan->g_obj, nO, plan->norm_part, kNormParts, plan->d_scal, 1, st));
-    CUDA_TRY(launch_norm2(plan->g_probe, nP, plan->norm_part, kNormParts, plan->d_scal, 2, st));
+    TIMED(K_OTHER, 2, launch_norm2(plan->g_obj, nO, plan->norm_part, kNormParts, plan->d_scal, 1, st));
+    TIMED(K_OTHER, 2, launch_norm2(plan->g_probe, nP, plan->norm_part, kNormParts, plan->d_scal, 2, st));
     CUDA_TRY(cudaMemcpyAsync(plan->h_scal, plan->d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     const double F0 = plan->h_scal[0];
@@ -439,8 +510,8 @@ int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptyc
     if (!accepted) t = 0.0;
   }
   if (t > 0.0) {
-    CUDA_TRY(launch_axpy(O, plan->g_obj, O, -t * alpha_obj, nO, st));
-    CUDA_TRY(launch_axpy(P, plan->g_probe, P, -t * alpha_probe, nP, st));
+    TIMED(K_OTHER, 1, launch_axpy(O, plan->g_obj, O, -t * alpha_obj, nO, st));
+    TIMED(K_OTHER, 1, launch_axpy(P, plan->g_probe, P, -t * alpha_probe, nP, st));
   }
   if (t_out) *t_out = t;
   return PTYCHO_OK;

@@ -9,6 +9,45 @@ from paper_2205_06327_gb300 import synth
 TOL_FP32 = 1e-5   # rel-L2 bound of the FP32 path against the FP64 oracle
 
 
+def c64(a):
+    """The complex64 values the GPU path receives, as complex128 for the oracle."""
+    return np.asarray(a).astype(np.complex64).astype(np.complex128)
+
+
+def fp32_chain_loss_grad(probe, obj, pos, I, h):
+    """The same chain evaluated with single-precision FFTs (SciPy) and complex64
+    pointwise arithmetic: an error model of plain FP32, not a reference value.
+    Used to state the rounding floor that FP32 arithmetic itself reaches."""
+    import scipy.fft as sf
+    M, S = probe.shape[0], obj.shape[0]
+    P, O, h32 = probe.astype(np.complex64), obj.astype(np.complex64), h.astype(np.complex64)
+    f = lambda x: sf.fft2(x, norm="ortho")
+    fi = lambda x: sf.ifft2(x, norm="ortho")
+    gO = np.zeros(obj.shape, np.complex64)
+    gP = np.zeros(probe.shape, np.complex64)
+    L = 0.0
+    for i, (y, x) in enumerate(pos):
+        psi, cur = [], P
+        for s in range(S):
+            psi.append(cur)
+            ph = cur * O[s, y:y + M, x:x + M]
+            if s < S - 1:
+                cur = fi(h32 * f(ph))
+        Psi = f(ph)
+        a = np.abs(Psi)
+        d = a - np.sqrt(I[i].astype(np.float32))
+        L += float(np.sum(d.astype(np.float64) ** 2))
+        g = np.where(a > 0, 2 * d * Psi / np.where(a > 0, a, 1), 0).astype(np.complex64)
+        gphi = fi(g)
+        for s in range(S - 1, -1, -1):
+            gO[s, y:y + M, x:x + M] += np.conj(psi[s]) * gphi
+            gpsi = np.conj(O[s, y:y + M, x:x + M]) * gphi
+            if s > 0:
+                gphi = fi(np.conj(h32) * f(gpsi))
+        gP += gpsi
+    return L, gO, gP
+
+
 def rel_l2(a, b) -> float:
     a = np.asarray(a, dtype=np.complex128)
     b = np.asarray(b, dtype=np.complex128)
