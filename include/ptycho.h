@@ -165,6 +165,37 @@ typedef struct {
 
 PTYCHO_API int ptycho_plan_timing(ptycho_plan plan, ptycho_timing* out, int32_t reset);
 
+/* Loss and gradients exactly as ptycho_loss_grad, for callers that cannot
+ * allocate device memory: code that runs inside a custom device allocator or
+ * a memory-pool callback (where calling cudaMalloc would re-enter it), or a
+ * process whose device allocations are fixed after start-up.  It allocates
+ * nothing -- no plan, no cudaMalloc/cudaFree, no allocating library call.
+ * The paper has no counterpart: this is the same kernels, differently fed.
+ *
+ * Scratch: one static device array of 64 MiB, held by every GPU that loads
+ * the library until the process exits.  Positions run in chunks that fit in
+ * it; a problem whose single position needs more than it holds (about
+ * (2S) * M * M * 8 bytes plus 4 MiB) returns PTYCHO_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address (and sets
+ * the kernels' shared-memory limit); make that first call before any stream
+ * capture.  Every call shares the array and keeps the previous call's
+ * contents (what must start at zero is cleared by each call): calls that
+ * overlap on the GPU -- two streams, two host threads, two devices sharing
+ * nothing else are fine only if they do not run at the same time on the same
+ * device -- race on it.
+ *   params     problem description (tile_h/tile_w as for plans; flags and
+ *              workspace_bytes are ignored)
+ *   pos_yx, probe, obj, meas_I, grad_obj, grad_probe: as ptycho_loss_grad
+ *   loss_out   double[1], device or host (required)
+ * Positions are checked on the device; the call then synchronises the stream
+ * and returns PTYCHO_ERR_POSITION if a window lay outside the object (that
+ * window contributes nothing).  Errors are reported by the return code only
+ * (ptycho_last_error() is not updated). */
+PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, const int32_t* pos_yx,
+                                        const ptycho_c64* probe, const ptycho_c64* obj,
+                                        const float* meas_I, double* loss_out, ptycho_c64* grad_obj,
+                                        ptycho_c64* grad_probe, void* stream);
+
 /* Text of the last error on the calling host thread ("" if none). */
 PTYCHO_API const char* ptycho_last_error(void);
 

@@ -35,8 +35,8 @@ ERROR_NAMES = {
 # Every symbol include/ptycho.h declares.
 EXPORTED = [
     "ptycho_plan_create", "ptycho_plan_destroy", "ptycho_plan_info", "ptycho_plan_status",
-    "ptycho_forward", "ptycho_loss_grad", "ptycho_step", "ptycho_plan_timing", "ptycho_last_error",
-    "ptycho_version",
+    "ptycho_forward", "ptycho_loss_grad", "ptycho_step", "ptycho_plan_timing", "ptycho_loss_grad_noalloc",
+    "ptycho_last_error", "ptycho_version",
 ]
 
 
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ptycho_loss_grad": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_step": ([vp, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp], C.c_int),
         "ptycho_plan_timing": ([vp, C.POINTER(PtychoTiming), i32], C.c_int),
+        "ptycho_loss_grad_noalloc": ([C.POINTER(PtychoParams), vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_last_error": ([], C.c_char_p),
         "ptycho_version": ([], C.c_char_p),
     }
