@@ -89,7 +89,7 @@ typedef struct {
                               are processed in chunks that fit the cap, so the
                               memory used does not grow with N. */
   int32_t tile_h, tile_w;  /* object-gradient accumulation tile (pixels);
-                              0 = 64 x 64.  tile_h * tile_w <= 8192. */
+                              0 = 32 x 32.  tile_h * tile_w <= 8192. */
 } ptycho_params;
 
 typedef struct ptycho_plan_s* ptycho_plan;

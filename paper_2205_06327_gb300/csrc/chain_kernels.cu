@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
 
   for (int s = 0; s < a.S; ++s) {
     if (MODE == MODE_GRAD && s > 0) {
-      float2* dst = a.ws_psi + ((size_t)il * (a.S - 1) + (s - 1)) * MM;
+      float2* dst = a.ws_psi + ((size_t)(s - 1) * a.ws_n + il) * MM;
       for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
     }
     const float2* ow = objw + (size_t)s * HW;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
     } else {
       fft_inv<C>(v, sm, tw, t);  // g_phi for the last slice
       for (int s = a.S - 1; s >= 0; --s) {
-        float2* dst = a.ws_gphi + ((size_t)il * a.S + s) * MM;
+        float2* dst = a.ws_gphi + ((size_t)s * a.ws_n + il) * MM;
         for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
         const float2* ow = objw + (size_t)s * HW;
         for_p0<C>(t, [&](int e, int py, int px) {

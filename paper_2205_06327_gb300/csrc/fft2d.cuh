@@ -23,6 +23,10 @@
 #include <cuda_runtime.h>
 #include <type_traits>
 
+#ifndef PTYCHO_TWIDDLE_FACTORED
+#define PTYCHO_TWIDDLE_FACTORED 1
+#endif
+
 namespace ptycho {
 
 template <int I, int N, class F>
@@ -247,6 +251,30 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[C::V], const float2* __
     }
     auto twiddle = [&]() {
       if constexpr (J < 2) {
+#if PTYCHO_TWIDDLE_FACTORED
+        // w^(ey a + ex b) = w^(ey a) * w^(ex b): RY-1 + RX-1 table reads and
+        // one extra product per element with a, b > 0.
+        float2 txv[P::RX];
+        static_for<1, P::RX>([&](auto bb) {
+          constexpr int b = decltype(bb)::value;
+          txv[b] = tw[(ex * b) & (C::M - 1)];
+        });
+        static_for<0, P::RY>([&](auto aa) {
+          constexpr int a = decltype(aa)::value;
+          float2 ty = make_float2(1.f, 0.f);
+          if constexpr (a != 0) ty = tw[(ey * a) & (C::M - 1)];
+          static_for<0, P::RX>([&](auto bb) {
+            constexpr int b = decltype(bb)::value;
+            if constexpr (a != 0 && b != 0) {
+              v[o + a * P::RX + b] = cmul_opt<INV>(v[o + a * P::RX + b], cmul(ty, txv[b]));
+            } else if constexpr (a != 0) {
+              v[o + a * P::RX + b] = cmul_opt<INV>(v[o + a * P::RX + b], ty);
+            } else if constexpr (b != 0) {
+              v[o + a * P::RX + b] = cmul_opt<INV>(v[o + a * P::RX + b], txv[b]);
+            }
+          });
+        });
+#else
         static_for<0, P::RY>([&](auto aa) {
           constexpr int a = decltype(aa)::value;
           static_for<0, P::RX>([&](auto bb) {
@@ -257,6 +285,7 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[C::V], const float2* __
             }
           });
         });
+#endif
       }
     };
     if constexpr (INV) twiddle();

@@ -24,9 +24,10 @@ struct ChainArgs {
   int S, H, W;
   const float2* tw;       // [M]   w_M^e = exp(-2 pi i e / M)
   const float2* hs;       // [M]   one separable factor of the propagator, times 1/M
-  float2* ws_psi;         // [n_pos][S-1][M][M] waves entering slices 1..S-1
-  float2* ws_gphi;        // [n_pos][S][M][M]   gradient w.r.t. each slice's exit wave
-  float2* ws_gp;          // [n_pos][M][M]      per-position probe gradient
+  int ws_n;               // positions the workspace holds (slice stride of ws_psi / ws_gphi)
+  float2* ws_psi;         // [S-1][ws_n][M][M] waves entering slices 1..S-1
+  float2* ws_gphi;        // [S][ws_n][M][M]   gradient w.r.t. each slice's exit wave
+  float2* ws_gp;          // [ws_n][M][M]      per-position probe gradient
   double* loss_part;      // [n_pos]
   float2* psi_out;        // [N][M][M] or null (forward mode)
   float* int_out;         // [N][M][M] or null (forward mode)
@@ -40,14 +41,16 @@ cudaError_t chain_prepare(int M);  // raise the dynamic shared-memory limit
 cudaError_t launch_chain(int M, ChainMode mode, const ChainArgs& a, cudaStream_t st);
 
 // reduce_kernels.cu
+constexpr int kDefaultTile = 32;  // default owner tile of the object-gradient accumulation
 struct AccumArgs {
   const int2* pos;
   int pos_begin, n_pos;
   int M, S, H, W;
   int tile_h, tile_w;
   const float2* probe;      // wave entering slice 0 (= probe)
-  const float2* ws_psi;
-  const float2* ws_gphi;
+  int ws_n;                 // slice stride (positions) of ws_psi / ws_gphi
+  const float2* ws_psi;     // [S-1][ws_n][M][M]
+  const float2* ws_gphi;    // [S][ws_n][M][M]
   float2* grad_obj;         // [S][H][W]
   int accumulate;           // 0: overwrite the whole gradient, 1: add
 };

@@ -67,7 +67,7 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
   if (p.S < 1 || p.H < p.M || p.W < p.M || p.N < 0 || p.precision != PTYCHO_FP32 || !(p.pixel_A > 0) ||
       !std::isfinite(p.lambda_A) || !std::isfinite(p.dz_A))
     return noalloc_fail(PTYCHO_ERR_ARG, "bad problem parameters");
-  const int th = p.tile_h ? p.tile_h : 64, tw_ = p.tile_w ? p.tile_w : 64;
+  const int th = p.tile_h ? p.tile_h : kDefaultTile, tw_ = p.tile_w ? p.tile_w : kDefaultTile;
   if (th < 1 || tw_ < 1 || th * tw_ > 8192) return noalloc_fail(PTYCHO_ERR_ARG, "tile_h * tile_w must be in [1, 8192]");
   if (!loss_out) return noalloc_fail(PTYCHO_ERR_ARG, "loss_out is NULL");
   if (!device_ptr(probe) || !device_ptr(obj) || (p.N > 0 && (!device_ptr(meas_I) || !device_ptr(pos_yx))) ||
@@ -159,6 +159,7 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
   a.W = p.W;
   a.tw = d_tw;
   a.hs = d_hs;
+  a.ws_n = chunk;
   a.ws_psi = ws_psi;
   a.ws_gphi = ws_gphi;
   a.ws_gp = ws_gp;
@@ -183,6 +184,7 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
       g.tile_h = th;
       g.tile_w = tw_;
       g.probe = a.probe;
+      g.ws_n = chunk;
       g.ws_psi = ws_psi;
       g.ws_gphi = ws_gphi;
       g.grad_obj = reinterpret_cast<float2*>(grad_obj);

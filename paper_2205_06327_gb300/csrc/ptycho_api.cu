@@ -131,7 +131,7 @@ int validate_params(const ptycho_params& p) {
   if (!(p.pixel_A > 0) || !std::isfinite(p.lambda_A) || !std::isfinite(p.dz_A))
     return fail(PTYCHO_ERR_ARG, "bad propagator parameters");
   if (p.workspace_bytes < 0) return fail(PTYCHO_ERR_ARG, "workspace_bytes must be >= 0");
-  const int th = p.tile_h ? p.tile_h : 64, tw = p.tile_w ? p.tile_w : 64;
+  const int th = p.tile_h ? p.tile_h : kDefaultTile, tw = p.tile_w ? p.tile_w : kDefaultTile;
   if (th < 1 || tw < 1 || th * tw > 8192) return fail(PTYCHO_ERR_ARG, "tile_h * tile_w must be in [1, 8192]");
   if ((int64_t)p.S * p.H * p.W > (int64_t)1 << 34) return fail(PTYCHO_ERR_ARG, "object too large");
   return PTYCHO_OK;
@@ -211,6 +211,7 @@ ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe,
   a.W = pl->p.W;
   a.tw = pl->d_tw;
   a.hs = pl->d_hs;
+  a.ws_n = pl->chunk;
   a.ws_psi = pl->ws_psi;
   a.ws_gphi = pl->ws_gphi;
   a.ws_gp = pl->ws_gp;
@@ -252,9 +253,10 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
       g.S = p.S;
       g.H = p.H;
       g.W = p.W;
-      g.tile_h = p.tile_h ? p.tile_h : 64;
-      g.tile_w = p.tile_w ? p.tile_w : 64;
+      g.tile_h = p.tile_h ? p.tile_h : kDefaultTile;
+      g.tile_w = p.tile_w ? p.tile_w : kDefaultTile;
       g.probe = a.probe;
+      g.ws_n = pl->chunk;
       g.ws_psi = pl->ws_psi;
       g.ws_gphi = pl->ws_gphi;
       g.grad_obj = grad_obj;

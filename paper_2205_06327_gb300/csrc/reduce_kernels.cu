@@ -20,9 +20,15 @@ __device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p);
 
 constexpr int kAccThreads = 256;
 
-template <int PPT>
-__global__ void __launch_bounds__(kAccThreads) k_accum_obj_grad(const AccumArgs a) {
-  __shared__ int list[kAccThreads];
+constexpr int kAccUnroll = 4;  // positions whose loads are in flight together
+constexpr int kAccPPT = 4;     // pixels per thread per pixel group
+
+// One block owns one (tile, slice).  The tile's pixels are processed in
+// groups of kAccPPT * 256; for each group the block walks the positions whose
+// window meets the group's rows, in ascending order.
+__global__ void __launch_bounds__(kAccThreads, 2) k_accum_obj_grad(const AccumArgs a) {
+  __shared__ int2 lpos[kAccThreads];
+  __shared__ int lidx[kAccThreads];
   __shared__ int wcount[kAccThreads / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int s = blockIdx.z;
@@ -30,81 +36,99 @@ __global__ void __launch_bounds__(kAccThreads) k_accum_obj_grad(const AccumArgs 
   const int ty0 = blockIdx.y * a.tile_h, tx0 = blockIdx.x * a.tile_w;
   const int th = min(a.tile_h, a.H - ty0), tw = min(a.tile_w, a.W - tx0);
   const int npix = th * tw;
-
-  int rowk[PPT], colk[PPT];
-  float2 acc[PPT];
-#pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    const int p = t + kAccThreads * k;
-    rowk[k] = p < npix ? p / tw : (1 << 28);
-    colk[k] = p < npix ? p % tw : 0;
-    acc[k] = make_float2(0.f, 0.f);
-  }
   const size_t MM = (size_t)M * M;
-
-  for (int base = 0; base < a.n_pos; base += kAccThreads) {
-    const int il = base + t;
-    bool hit = false;
-    if (il < a.n_pos) {
-      const int2 r = a.pos[a.pos_begin + il];
-      const bool ok = r.x >= 0 && r.y >= 0 && r.x <= a.H - M && r.y <= a.W - M;
-      hit = ok && r.x < ty0 + th && r.x + M > ty0 && r.y < tx0 + tw && r.y + M > tx0;
-    }
-    const unsigned b = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) wcount[w] = __popc(b);
-    __syncthreads();
-    int off = 0, total = 0;
-#pragma unroll
-    for (int k = 0; k < kAccThreads / 32; ++k) {
-      off += k < w ? wcount[k] : 0;
-      total += wcount[k];
-    }
-    if (hit) list[off + __popc(b & ((1u << lane) - 1u))] = il;
-    __syncthreads();
-    for (int j = 0; j < total; ++j) {
-      const int i = list[j];
-      const int2 r = a.pos[a.pos_begin + i];
-      const int oy0 = ty0 - r.x, ox0 = tx0 - r.y;
-      const float2* gph = a.ws_gphi + ((size_t)i * a.S + s) * MM;
-      if (s == 0) {
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          const int oy = oy0 + rowk[k], ox = ox0 + colk[k];
-          if ((unsigned)oy < (unsigned)M && (unsigned)ox < (unsigned)M) {
-            const int idx = oy * M + ox;
-            const float2 p = __ldg(a.probe + idx), g = ld_stream(gph + idx);
-            acc[k].x = fmaf(p.x, g.x, fmaf(p.y, g.y, acc[k].x));
-            acc[k].y = fmaf(p.x, g.y, fmaf(-p.y, g.x, acc[k].y));
-          }
-        }
-      } else {
-        const float2* psi = a.ws_psi + ((size_t)i * (a.S - 1) + (s - 1)) * MM;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          const int oy = oy0 + rowk[k], ox = ox0 + colk[k];
-          if ((unsigned)oy < (unsigned)M && (unsigned)ox < (unsigned)M) {
-            const int idx = oy * M + ox;
-            const float2 p = ld_stream(psi + idx), g = ld_stream(gph + idx);
-            acc[k].x = fmaf(p.x, g.x, fmaf(p.y, g.y, acc[k].x));
-            acc[k].y = fmaf(p.x, g.y, fmaf(-p.y, g.x, acc[k].y));
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
+  const float2* gphi_s = a.ws_gphi + (size_t)s * a.ws_n * MM;
+  const float2* psi_s = s > 0 ? a.ws_psi + (size_t)(s - 1) * a.ws_n * MM : nullptr;
   float2* out = a.grad_obj + (size_t)s * a.H * a.W;
+  constexpr int GROUP = kAccPPT * kAccThreads;
+
+  for (int pg0 = 0; pg0 < npix; pg0 += GROUP) {
+    // Pixel k of this thread: p = pg0 + t + 256 k in the tile, row-major.
+    int rowk[kAccPPT], colk[kAccPPT];
+    float2 acc[kAccPPT];
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    if (rowk[k] < th) {
-      float2* o = out + (size_t)(ty0 + rowk[k]) * a.W + (tx0 + colk[k]);
-      float2 val = acc[k];
-      if (a.accumulate) {
-        const float2 prev = *o;
-        val.x += prev.x;
-        val.y += prev.y;
+    for (int k = 0; k < kAccPPT; ++k) {
+      const int p = pg0 + t + kAccThreads * k;
+      rowk[k] = p < npix ? p / tw : (1 << 28);
+      colk[k] = p < npix ? p % tw : 0;
+      acc[k] = make_float2(0.f, 0.f);
+    }
+    const int gy0 = ty0 + pg0 / tw;
+    const int gy1 = ty0 + min(npix - 1, pg0 + GROUP - 1) / tw + 1;  // rows [gy0, gy1)
+
+    for (int base = 0; base < a.n_pos; base += kAccThreads) {
+      // Positions of this batch whose window meets the group, compacted in
+      // ascending order (ballot + warp prefix): the summation order.
+      const int il = base + t;
+      bool hit = false;
+      int2 r = make_int2(0, 0);
+      if (il < a.n_pos) {
+        r = a.pos[a.pos_begin + il];
+        const bool ok = r.x >= 0 && r.y >= 0 && r.x <= a.H - M && r.y <= a.W - M;
+        hit = ok && r.x < gy1 && r.x + M > gy0 && r.y < tx0 + tw && r.y + M > tx0;
       }
-      *o = val;
+      const unsigned b = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) wcount[w] = __popc(b);
+      __syncthreads();
+      int off = 0, total = 0;
+#pragma unroll
+      for (int k = 0; k < kAccThreads / 32; ++k) {
+        off += k < w ? wcount[k] : 0;
+        total += wcount[k];
+      }
+      if (hit) {
+        const int slot = off + __popc(b & ((1u << lane) - 1u));
+        lpos[slot] = r;
+        lidx[slot] = il;
+      }
+      __syncthreads();
+      for (int j0 = 0; j0 < total; j0 += kAccUnroll) {
+        // Issue the loads of up to kAccUnroll positions, then add them in
+        // order.  Pixels outside a window load zeros, whose product adds
+        // exactly nothing.
+        float2 pv[kAccUnroll][kAccPPT], gv[kAccUnroll][kAccPPT];
+#pragma unroll
+        for (int u = 0; u < kAccUnroll; ++u) {
+          const int j = j0 + u;
+          const bool live = j < total;
+          const int2 rr = lpos[live ? j : 0];
+          const int i = lidx[live ? j : 0];
+          const int oy0 = ty0 - rr.x, ox0 = tx0 - rr.y;
+          const float2* gp = gphi_s + (size_t)i * MM;
+          const float2* pp = s > 0 ? psi_s + (size_t)i * MM : a.probe;
+#pragma unroll
+          for (int k = 0; k < kAccPPT; ++k) {
+            const int oy = oy0 + rowk[k], ox = ox0 + colk[k];
+            const bool in = live && (unsigned)oy < (unsigned)M && (unsigned)ox < (unsigned)M;
+            const int idx = in ? oy * M + ox : 0;
+            pv[u][k] = in ? (s > 0 ? ld_stream(pp + idx) : __ldg(pp + idx)) : make_float2(0.f, 0.f);
+            gv[u][k] = in ? ld_stream(gp + idx) : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kAccUnroll; ++u) {
+#pragma unroll
+          for (int k = 0; k < kAccPPT; ++k) {
+            const float2 p = pv[u][k], g = gv[u][k];
+            acc[k].x = fmaf(p.x, g.x, fmaf(p.y, g.y, acc[k].x));
+            acc[k].y = fmaf(p.x, g.y, fmaf(-p.y, g.x, acc[k].y));
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < kAccPPT; ++k) {
+      if (rowk[k] < th) {
+        float2* o = out + (size_t)(ty0 + rowk[k]) * a.W + (tx0 + colk[k]);
+        float2 val = acc[k];
+        if (a.accumulate) {
+          const float2 prev = *o;
+          val.x += prev.x;
+          val.y += prev.y;
+        }
+        *o = val;
+      }
     }
   }
 }
@@ -190,11 +214,7 @@ __global__ void k_check_positions(const int2* __restrict__ pos, int n, int M, in
 
 cudaError_t launch_accum_obj_grad(const AccumArgs& a, cudaStream_t st) {
   const dim3 grid((a.W + a.tile_w - 1) / a.tile_w, (a.H + a.tile_h - 1) / a.tile_h, a.S);
-  const int npix = a.tile_h * a.tile_w;
-  if (npix <= 16 * kAccThreads)
-    k_accum_obj_grad<16><<<grid, kAccThreads, 0, st>>>(a);
-  else
-    k_accum_obj_grad<32><<<grid, kAccThreads, 0, st>>>(a);
+  k_accum_obj_grad<<<grid, kAccThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
