@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
   const size_t MM = (size_t)M * M;
   const size_t HW = (size_t)a.H * a.W;
   const float2* objw = a.obj + (size_t)yi * a.W + xi;
-  const float2* dirw = a.obj_dir ? a.obj_dir + (size_t)yi * a.W + xi : nullptr;
+  // (gradient mode always evaluates at obj itself)
+  const float2* dirw = (MODE != MODE_GRAD && a.obj_dir) ? a.obj_dir + (size_t)yi * a.W + xi : nullptr;
 
   float2 v[C::V];
   // psi_0 = P
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
       float2* dst = a.ws_psi + ((size_t)(s - 1) * a.ws_n + il) * MM;
       for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
     }
+    // phi_s = psi_s * O_s[window]  (O + step * dir during a line search)
     const float2* ow = objw + (size_t)s * HW;
     const float2* dw = dirw ? dirw + (size_t)s * HW : nullptr;
     for_p0<C>(t, [&](int e, int py, int px) {
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
     if constexpr (MODE == MODE_LOSS) {
       return;
     } else {
-      fft_inv<C>(v, sm, tw, t);  // g_phi for the last slice
+      fft_inv<C, true>(v, sm, tw, t);  // g_phi for the last slice
       for (int s = a.S - 1; s >= 0; --s) {
         float2* dst = a.ws_gphi + ((size_t)s * a.ws_n + il) * MM;
         for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
@@ -181,9 +183,9 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
           v[e] = cmulc(v[e], ldg2(ow + (size_t)py * a.W + px));  // g_psi = conj(O) g_phi
         });
         if (s > 0) {
-          fft_fwd<C>(v, sm, tw, t);
+          fft_fwd<C, true>(v, sm, tw, t);
           mul_separable<C, true>(v, hs, t);
-          fft_inv<C>(v, sm, tw, t);
+          fft_inv<C, true>(v, sm, tw, t);
         }
       }
       float2* gp = a.ws_gp + (size_t)il * MM;

@@ -23,10 +23,6 @@
 #include <cuda_runtime.h>
 #include <type_traits>
 
-#ifndef PTYCHO_TWIDDLE_FACTORED
-#define PTYCHO_TWIDDLE_FACTORED 1
-#endif
-
 namespace ptycho {
 
 template <int I, int N, class F>
@@ -130,6 +126,11 @@ struct Cfg<128> {
   static constexpr int sy(int j) { return j == 0 ? 16 : (j == 1 ? 4 : 1); }
   static constexpr int sx(int j) { return j == 0 ? 32 : (j == 1 ? 4 : 1); }
   __device__ static __forceinline__ int swz(int px) { return px ^ (5 * ((px >> 5) & 3)); }
+  // The pass-1 <-> pass-2 exchange stays inside warp pairs {2k, 2k+1}: a
+  // 64-thread named barrier (ids 1..8) orders it.
+  __device__ static __forceinline__ void sync12(int t) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + (t >> 6)) : "memory");
+  }
   template <int J>
   __device__ static __forceinline__ void base(int t, int q, int& py, int& px) {
     const int w = t >> 5, l = t & 31;
@@ -154,6 +155,8 @@ struct Cfg<64> {
   static constexpr int sy(int j) { return j == 0 ? 16 : (j == 1 ? 4 : 1); }
   static constexpr int sx(int j) { return j == 0 ? 16 : (j == 1 ? 4 : 1); }
   __device__ static __forceinline__ int swz(int px) { return px ^ (5 * ((px >> 4) & 3)); }
+  // The pass-1 <-> pass-2 exchange stays inside each warp.
+  __device__ static __forceinline__ void sync12(int) { __syncwarp(); }
   template <int J>
   __device__ static __forceinline__ void base(int t, int q, int& py, int& px) {
     const int w = t >> 5, l = t & 31;
@@ -235,7 +238,11 @@ __device__ __forceinline__ void xch_load(float2 (&v)[C::V], const float2* sm, in
 // x element), DFT over digit J of x (for every y element), then the twiddle
 // w_M^(ey*a' + ex*b') that couples digit J to the lower digits.  Inverse: the
 // conjugate twiddle, then the inverse DFTs (exact inverse up to the factor RY*RX).
-template <class C, int J, bool INV>
+// FACT selects factored twiddles w^(ey a) * w^(ex b): fewer table reads but
+// one more rounding per element.  The forward model (whose rounding the
+// amplitude residual amplifies) uses exact table values; the adjoint, which
+// is linear in the residual, uses the factored form.
+template <class C, int J, bool INV, bool FACT = false>
 __device__ __forceinline__ void pass_compute(float2 (&v)[C::V], const float2* __restrict__ tw, int t) {
   using P = PassShape<C, J>;
   t = opaque(t);
@@ -250,8 +257,7 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[C::V], const float2* __
       ex = (C::M / (P::RX * P::SX)) * (px & (P::SX - 1));
     }
     auto twiddle = [&]() {
-      if constexpr (J < 2) {
-#if PTYCHO_TWIDDLE_FACTORED
+      if constexpr (J < 2 && FACT) {
         // w^(ey a + ex b) = w^(ey a) * w^(ex b): RY-1 + RX-1 table reads and
         // one extra product per element with a, b > 0.
         float2 txv[P::RX];
@@ -274,7 +280,7 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[C::V], const float2* __
             }
           });
         });
-#else
+      } else if constexpr (J < 2) {
         static_for<0, P::RY>([&](auto aa) {
           constexpr int a = decltype(aa)::value;
           static_for<0, P::RX>([&](auto bb) {
@@ -285,7 +291,6 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[C::V], const float2* __
             }
           });
         });
-#endif
       }
     };
     if constexpr (INV) twiddle();
@@ -303,32 +308,32 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[C::V], const float2* __
 
 // registers in pass-0 grouping (natural storage) -> unnormalised forward DFT,
 // registers in pass-2 grouping (digit-reversed storage)
-template <class C>
+template <class C, bool FACT = false>
 __device__ __forceinline__ void fft_fwd(float2 (&v)[C::V], float2* sm, const float2* tw, int t) {
-  pass_compute<C, 0, false>(v, tw, t);
+  pass_compute<C, 0, false, FACT>(v, tw, t);
   xch_store<C, 0>(v, sm, t);
   __syncthreads();
   xch_load<C, 1>(v, sm, t);
-  pass_compute<C, 1, false>(v, tw, t);
+  pass_compute<C, 1, false, FACT>(v, tw, t);
   xch_store<C, 1>(v, sm, t);
-  __syncthreads();
+  C::sync12(t);
   xch_load<C, 2>(v, sm, t);
-  pass_compute<C, 2, false>(v, tw, t);
+  pass_compute<C, 2, false, FACT>(v, tw, t);
 }
 
 // exact reverse of fft_fwd: unnormalised inverse DFT (times M*M relative to
 // the true inverse), registers back in pass-0 grouping
-template <class C>
+template <class C, bool FACT = false>
 __device__ __forceinline__ void fft_inv(float2 (&v)[C::V], float2* sm, const float2* tw, int t) {
-  pass_compute<C, 2, true>(v, tw, t);
+  pass_compute<C, 2, true, FACT>(v, tw, t);
   xch_store<C, 2>(v, sm, t);
-  __syncthreads();
+  C::sync12(t);
   xch_load<C, 1>(v, sm, t);
-  pass_compute<C, 1, true>(v, tw, t);
+  pass_compute<C, 1, true, FACT>(v, tw, t);
   xch_store<C, 1>(v, sm, t);
   __syncthreads();
   xch_load<C, 0>(v, sm, t);
-  pass_compute<C, 0, true>(v, tw, t);
+  pass_compute<C, 0, true, FACT>(v, tw, t);
 }
 
 // Multiply the spectrum (pass-2 grouping) by h(ky)*h(kx) (or its conjugate);
