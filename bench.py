@@ -294,7 +294,7 @@ def run_gpu(args, world, rank, local, pool):
     tile = (0, 0)
     if args.config == 3:
         tile = ((wl.H + 7) // 8, (wl.W + 7) // 8)  # 8 x 8 tessellation of the gradient
-    plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile)
+    plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=args.ckpt_every)
     pos = torch.from_numpy(wl.pos).to(device)
     probe = torch.from_numpy(wl.probe.astype(np.complex64)).to(device)
     obj_true = torch.from_numpy(wl.obj.astype(np.complex64)).to(device)
@@ -399,7 +399,8 @@ def run_gpu(args, world, rank, local, pool):
         "config": {"workload": wl.name, "positions": wl.N, "M": wl.M, "S": wl.S, "object": [wl.H, wl.W],
                    "tiles": list(tile) if tile != (0, 0) else [64, 64],
                    "l2": "flushed between timed steps (512 MiB write, outside the step events)",
-                   "replicas": world, "wall_s": wall},
+                   "replicas": world, "wall_s": wall, "ckpt_every": args.ckpt_every,
+                   "workspace_bytes": plan.workspace_bytes, "chunk": plan.chunk},
         "roofline": {"bound": "alu", "kernel": "k_chain (slice chain, gradient mode)",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
@@ -433,6 +434,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=576)
     ap.add_argument("--positions", type=int, default=0, help="first N positions only (profiling cases)")
+    ap.add_argument("--ckpt-every", type=int, default=0,
+                    help="recompute mode: keep a wave checkpoint every L slices (0 = keep all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)

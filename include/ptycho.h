@@ -90,6 +90,13 @@ typedef struct {
                               memory used does not grow with N. */
   int32_t tile_h, tile_w;  /* object-gradient accumulation tile (pixels);
                               0 = 32 x 32.  tile_h * tile_w <= 8192. */
+  int32_t ckpt_every; /* 0: keep every slice's wave for the adjoint (fastest).
+                         L >= 1: keep a checkpoint every L slices and recompute
+                         each segment's waves during the adjoint; the workspace
+                         per position drops from (2S-1) to S + ceil(S/L) + L + 1
+                         wave-sized buffers and the gradient accumulation reads
+                         half the bytes, for about (S - ceil(S/L)) / (2S - 1)
+                         more FFT work.  L = 0 is used when L >= S. */
 } ptycho_params;
 
 typedef struct ptycho_plan_s* ptycho_plan;
@@ -195,6 +202,18 @@ PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, const int32
                                         const ptycho_c64* probe, const ptycho_c64* obj,
                                         const float* meas_I, double* loss_out, ptycho_c64* grad_obj,
                                         ptycho_c64* grad_probe, void* stream);
+
+/* Potential parameterisation.  The paper's unknown is the real scattering
+ * potential V (Sec. II-B, Eq. 1); the slices transmit O = exp(i sigma V).
+ * ptycho_potential_to_transmission: obj[k] = exp(i sigma V[k]), k < n.
+ * ptycho_potential_grad: grad_V[k] = sigma * Im(conj(obj[k]) * grad_obj[k]),
+ * the chain rule of dF/dO through O = exp(i sigma V) (with the gradient
+ * convention above), so that gradient descent can update V directly.
+ *   V, grad_V   float [n] device;  obj, grad_obj  c64 [n] device (e.g. [S][H][W]) */
+PTYCHO_API int ptycho_potential_to_transmission(const float* V, ptycho_c64* obj, int64_t n, double sigma,
+                                                void* stream);
+PTYCHO_API int ptycho_potential_grad(const ptycho_c64* obj, const ptycho_c64* grad_obj, float* grad_V, int64_t n,
+                                     double sigma, void* stream);
 
 /* Text of the last error on the calling host thread ("" if none). */
 PTYCHO_API const char* ptycho_last_error(void);

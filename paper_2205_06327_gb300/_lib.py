@@ -36,7 +36,7 @@ ERROR_NAMES = {
 EXPORTED = [
     "ptycho_plan_create", "ptycho_plan_destroy", "ptycho_plan_info", "ptycho_plan_status",
     "ptycho_forward", "ptycho_loss_grad", "ptycho_step", "ptycho_plan_timing", "ptycho_loss_grad_noalloc",
-    "ptycho_last_error", "ptycho_version",
+    "ptycho_potential_to_transmission", "ptycho_potential_grad", "ptycho_last_error", "ptycho_version",
 ]
 
 
@@ -47,6 +47,7 @@ class PtychoParams(C.Structure):
         ("precision", C.c_int32), ("flags", C.c_int32),
         ("workspace_bytes", C.c_int64),
         ("tile_h", C.c_int32), ("tile_w", C.c_int32),
+        ("ckpt_every", C.c_int32),
     ]
 
 
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ptycho_step": ([vp, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp], C.c_int),
         "ptycho_plan_timing": ([vp, C.POINTER(PtychoTiming), i32], C.c_int),
         "ptycho_loss_grad_noalloc": ([C.POINTER(PtychoParams), vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "ptycho_potential_to_transmission": ([vp, vp, C.c_int64, dbl, vp], C.c_int),
+        "ptycho_potential_grad": ([vp, vp, vp, C.c_int64, dbl, vp], C.c_int),
         "ptycho_last_error": ([], C.c_char_p),
         "ptycho_version": ([], C.c_char_p),
     }

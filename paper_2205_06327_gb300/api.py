@@ -47,7 +47,7 @@ class Plan:
 
     def __init__(self, geom: Geometry, device: torch.device | int | str = "cuda",
                  workspace_bytes: int = 0, tile: tuple[int, int] = (0, 0), async_check: bool = False,
-                 timing: bool = False):
+                 timing: bool = False, ckpt_every: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("libptycho needs a CUDA device; there is no CPU fallback")
         self.lib = _lib.load()
@@ -62,6 +62,7 @@ class Plan:
         p.flags = (_lib.PTYCHO_FLAG_ASYNC_CHECK if async_check else 0) | (_lib.PTYCHO_FLAG_TIMING if timing else 0)
         p.workspace_bytes = int(workspace_bytes)
         p.tile_h, p.tile_w = int(tile[0]), int(tile[1])
+        p.ckpt_every = int(ckpt_every)
         self._params = p
         h = C.c_void_p()
         with torch.cuda.device(self.device):
@@ -176,3 +177,31 @@ class Plan:
 
 def version() -> str:
     return _lib.load().ptycho_version().decode()
+
+
+def potential_to_transmission(V: torch.Tensor, sigma: float = 1.0) -> torch.Tensor:
+    """O = exp(i sigma V) on the device (V float32, any shape)."""
+    if not V.is_cuda or V.dtype != torch.float32:
+        raise TypeError("V must be a float32 CUDA tensor")
+    V = V.contiguous()
+    O = torch.empty(V.shape, dtype=torch.complex64, device=V.device)
+    lib = _lib.load()
+    with torch.cuda.device(V.device):
+        check(lib.ptycho_potential_to_transmission(V.data_ptr(), O.data_ptr(), V.numel(), float(sigma),
+                                                   _stream_handle(V.device)))
+    return O
+
+
+def potential_grad(obj: torch.Tensor, grad_obj: torch.Tensor, sigma: float = 1.0) -> torch.Tensor:
+    """dF/dV = sigma * Im(conj(O) dF/dO) on the device."""
+    if not (obj.is_cuda and grad_obj.is_cuda) or obj.dtype != torch.complex64 or grad_obj.dtype != torch.complex64:
+        raise TypeError("obj and grad_obj must be complex64 CUDA tensors")
+    if obj.shape != grad_obj.shape:
+        raise ValueError("obj and grad_obj must have the same shape")
+    obj, grad_obj = obj.contiguous(), grad_obj.contiguous()
+    gV = torch.empty(obj.shape, dtype=torch.float32, device=obj.device)
+    lib = _lib.load()
+    with torch.cuda.device(obj.device):
+        check(lib.ptycho_potential_grad(obj.data_ptr(), grad_obj.data_ptr(), gV.data_ptr(), obj.numel(),
+                                        float(sigma), _stream_handle(obj.device)))
+    return gV

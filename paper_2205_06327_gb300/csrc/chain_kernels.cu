@@ -97,7 +97,10 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
   const size_t HW = (size_t)a.H * a.W;
   const float2* objw = a.obj + (size_t)yi * a.W + xi;
   // (gradient mode always evaluates at obj itself)
-  const float2* dirw = (MODE != MODE_GRAD && a.obj_dir) ? a.obj_dir + (size_t)yi * a.W + xi : nullptr;
+  constexpr bool GRAD = MODE == MODE_GRAD || MODE == MODE_GRAD_RC;
+  const float2* dirw = (!GRAD && a.obj_dir) ? a.obj_dir + (size_t)yi * a.W + xi : nullptr;
+  const int L = MODE == MODE_GRAD_RC ? a.ckpt_L : 1;
+  const int K = (a.S + L - 1) / L;  // segments (recompute mode)
 
   float2 v[C::V];
   // psi_0 = P
@@ -114,6 +117,10 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
   for (int s = 0; s < a.S; ++s) {
     if (MODE == MODE_GRAD && s > 0) {
       float2* dst = a.ws_psi + ((size_t)(s - 1) * a.ws_n + il) * MM;
+      for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
+    }
+    if (MODE == MODE_GRAD_RC && s > 0 && s % L == 0) {  // checkpoint entering segment s / L
+      float2* dst = a.ws_psi + ((size_t)(s / L - 1) * a.ws_n + il) * MM;
       for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
     }
     // phi_s = psi_s * O_s[window]  (O + step * dir during a line search)
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
     }
     if constexpr (MODE == MODE_LOSS) {
       return;
-    } else {
+    } else if constexpr (MODE == MODE_GRAD) {
       fft_inv<C, true>(v, sm, tw, t);  // g_phi for the last slice
       for (int s = a.S - 1; s >= 0; --s) {
         float2* dst = a.ws_gphi + ((size_t)s * a.ws_n + il) * MM;
@@ -188,6 +195,51 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
           fft_inv<C, true>(v, sm, tw, t);
         }
       }
+    } else {
+      // Recompute mode: per segment [s0, s1), park the adjoint state, rebuild
+      // the segment's entering waves from its checkpoint (the forward model's
+      // exact operations, so the same values), then run the adjoint through the
+      // segment writing the finished gradient patches.
+      fft_inv<C, true>(v, sm, tw, t);
+      float2* park = a.ws_psi + ((size_t)(K - 1 + L) * a.ws_n + il) * MM;
+      for (int j = K - 1; j >= 0; --j) {
+        const int s0 = j * L, s1 = min(s0 + L, a.S);
+        for_p0<C>(t, [&](int e, int py, int px) { park[py * M + px] = v[e]; });
+        if (j == 0) {
+          for_p0<C>(t, [&](int e, int py, int px) { v[e] = ldg2(a.probe + py * M + px); });
+        } else {  // written by this thread earlier in this kernel: coherent loads
+          const float2* ck = a.ws_psi + ((size_t)(j - 1) * a.ws_n + il) * MM;
+          for_p0<C>(t, [&](int e, int py, int px) { v[e] = ck[py * M + px]; });
+        }
+        for (int s = s0; s < s1; ++s) {
+          float2* seg = a.ws_psi + ((size_t)(K - 1 + (s - s0)) * a.ws_n + il) * MM;
+          for_p0<C>(t, [&](int e, int py, int px) { seg[py * M + px] = v[e]; });
+          if (s < s1 - 1) {
+            const float2* ow = objw + (size_t)s * HW;
+            for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmul(v[e], ldg2(ow + (size_t)py * a.W + px)); });
+            fft_fwd<C>(v, sm, tw, t);
+            mul_separable<C, false>(v, hs, t);
+            fft_inv<C>(v, sm, tw, t);
+          }
+        }
+        for_p0<C>(t, [&](int e, int py, int px) { v[e] = park[py * M + px]; });
+        for (int s = s1 - 1; s >= s0; --s) {
+          const float2* seg = a.ws_psi + ((size_t)(K - 1 + (s - s0)) * a.ws_n + il) * MM;
+          float2* patch = a.ws_gphi + ((size_t)s * a.ws_n + il) * MM;
+          for_p0<C>(t, [&](int e, int py, int px) {
+            __stcs(patch + py * M + px, cconjmul(seg[py * M + px], v[e]));  // conj(psi_s) g_phi_s
+          });
+          const float2* ow = objw + (size_t)s * HW;
+          for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmulc(v[e], ldg2(ow + (size_t)py * a.W + px)); });
+          if (s > 0) {
+            fft_fwd<C, true>(v, sm, tw, t);
+            mul_separable<C, true>(v, hs, t);
+            fft_inv<C, true>(v, sm, tw, t);
+          }
+        }
+      }
+    }
+    if constexpr (GRAD) {
       float2* gp = a.ws_gp + (size_t)il * MM;
       for_p0<C>(t, [&](int e, int py, int px) { __stcs(gp + py * M + px, v[e]); });
     }
@@ -207,6 +259,7 @@ static cudaError_t prepare_m() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_chain<M, MODE_FORWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_chain<M, MODE_LOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_chain<M, MODE_GRAD_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_chain<M, MODE_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -219,6 +272,7 @@ static cudaError_t launch_m(ChainMode mode, const ChainArgs& a, cudaStream_t st)
   switch (mode) {
     case MODE_FORWARD: k_chain<M, MODE_FORWARD><<<grid, block, smem, st>>>(a); break;
     case MODE_LOSS: k_chain<M, MODE_LOSS><<<grid, block, smem, st>>>(a); break;
+    case MODE_GRAD_RC: k_chain<M, MODE_GRAD_RC><<<grid, block, smem, st>>>(a); break;
     default: k_chain<M, MODE_GRAD><<<grid, block, smem, st>>>(a); break;
   }
   return cudaGetLastError();

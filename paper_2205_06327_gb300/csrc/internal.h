@@ -7,7 +7,11 @@
 
 namespace ptycho {
 
-enum ChainMode { MODE_FORWARD = 0, MODE_LOSS = 1, MODE_GRAD = 2 };
+// MODE_GRAD stores every slice's entering wave and exit-wave gradient;
+// MODE_GRAD_RC (recompute) stores checkpoints every ckpt_L slices, recomputes
+// each segment's waves during the adjoint and writes finished gradient
+// patches conj(psi_s) g_phi_s.
+enum ChainMode { MODE_FORWARD = 0, MODE_LOSS = 1, MODE_GRAD = 2, MODE_GRAD_RC = 3 };
 
 // Arguments of the per-position slice-chain kernel.  Positions
 // [pos_begin, pos_begin + n_pos) of the call are processed, one per block.
@@ -25,8 +29,11 @@ struct ChainArgs {
   const float2* tw;       // [M]   w_M^e = exp(-2 pi i e / M)
   const float2* hs;       // [M]   one separable factor of the propagator, times 1/M
   int ws_n;               // positions the workspace holds (slice stride of ws_psi / ws_gphi)
-  float2* ws_psi;         // [S-1][ws_n][M][M] waves entering slices 1..S-1
-  float2* ws_gphi;        // [S][ws_n][M][M]   gradient w.r.t. each slice's exit wave
+  int ckpt_L;             // recompute mode: checkpoint every ckpt_L slices
+  float2* ws_psi;         // GRAD: [S-1][ws_n][M][M] waves entering slices 1..S-1
+                          // GRAD_RC: [K-1 checkpoints | ckpt_L segment | 1 park][ws_n][M][M]
+  float2* ws_gphi;        // GRAD: [S][ws_n][M][M] gradient w.r.t. each slice's exit wave
+                          // GRAD_RC: [S][ws_n][M][M] gradient patches conj(psi_s) g_phi_s
   float2* ws_gp;          // [ws_n][M][M]      per-position probe gradient
   double* loss_part;      // [n_pos]
   float2* psi_out;        // [N][M][M] or null (forward mode)
@@ -53,6 +60,7 @@ struct AccumArgs {
   const float2* ws_gphi;    // [S][ws_n][M][M]
   float2* grad_obj;         // [S][H][W]
   int accumulate;           // 0: overwrite the whole gradient, 1: add
+  int patch_mode;           // 1: ws_gphi holds finished patches (ws_psi unused)
 };
 cudaError_t launch_accum_obj_grad(const AccumArgs& a, cudaStream_t st);
 cudaError_t launch_probe_grad(const float2* ws_gp, int n_pos, int M, float2* part, int n_split,
@@ -63,6 +71,9 @@ cudaError_t launch_axpy(float2* y, const float2* x, const float2* base, double a
                         cudaStream_t st);  // y = base + alpha * x
 cudaError_t launch_norm2(const float2* x, size_t n, double* part, int n_part, double* out,
                          int slot, cudaStream_t st);
+cudaError_t launch_potential_to_transmission(const float* V, float2* O, double sigma, size_t n, cudaStream_t st);
+cudaError_t launch_potential_grad(const float2* O, const float2* g, float* gV, double sigma, size_t n,
+                                  cudaStream_t st);
 cudaError_t launch_check_positions(const int2* pos, int n, int M, int H, int W, int* status,
                                    cudaStream_t st);
 

@@ -56,6 +56,7 @@ struct ptycho_plan_s {
   int device = 0;
   int sm_count = 0;
   int chunk = 0;             // positions per chunk
+  int ckpt_L = 0;            // recompute segment length (0 = keep every wave)
   int64_t ws_bytes = 0;
   float2* d_tw = nullptr;     // [M]
   float2* d_hs = nullptr;     // [M]
@@ -134,6 +135,7 @@ int validate_params(const ptycho_params& p) {
   const int th = p.tile_h ? p.tile_h : kDefaultTile, tw = p.tile_w ? p.tile_w : kDefaultTile;
   if (th < 1 || tw < 1 || th * tw > 8192) return fail(PTYCHO_ERR_ARG, "tile_h * tile_w must be in [1, 8192]");
   if ((int64_t)p.S * p.H * p.W > (int64_t)1 << 34) return fail(PTYCHO_ERR_ARG, "object too large");
+  if (p.ckpt_every < 0) return fail(PTYCHO_ERR_ARG, "ckpt_every must be >= 0");
   return PTYCHO_OK;
 }
 
@@ -212,6 +214,7 @@ ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe,
   a.tw = pl->d_tw;
   a.hs = pl->d_hs;
   a.ws_n = pl->chunk;
+  a.ckpt_L = pl->ckpt_L;
   a.ws_psi = pl->ws_psi;
   a.ws_gphi = pl->ws_gphi;
   a.ws_gp = pl->ws_gp;
@@ -242,7 +245,8 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     const int n = p.N - c0 < pl->chunk ? p.N - c0 : pl->chunk;
     a.pos_begin = c0;
     a.n_pos = n;
-    TIMED(K_CHAIN, 1, launch_chain(p.M, want_grad ? MODE_GRAD : MODE_LOSS, a, st));
+    const ChainMode mode = !want_grad ? MODE_LOSS : (pl->ckpt_L ? MODE_GRAD_RC : MODE_GRAD);
+    TIMED(K_CHAIN, 1, launch_chain(p.M, mode, a, st));
     pl->tm.chain_positions += n;
     if (grad_obj) {
       AccumArgs g{};
@@ -261,6 +265,7 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
       g.ws_gphi = pl->ws_gphi;
       g.grad_obj = grad_obj;
       g.accumulate = ci > 0;
+      g.patch_mode = pl->ckpt_L ? 1 : 0;
       TIMED(K_ACCUM, 1, launch_accum_obj_grad(g, st));
     }
     if (grad_probe)
@@ -326,7 +331,10 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
 
   // Workspace per position in flight (gradient mode).
   const size_t MM = (size_t)M * M;
-  const size_t per_pos = (size_t)(2 * p.S - 1) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
+  pl->ckpt_L = (p.ckpt_every > 0 && p.ckpt_every < p.S) ? p.ckpt_every : 0;
+  const int K = pl->ckpt_L ? (p.S + pl->ckpt_L - 1) / pl->ckpt_L : 0;
+  const size_t psi_slots = pl->ckpt_L ? (size_t)(K - 1 + pl->ckpt_L + 1) : (size_t)(p.S - 1);
+  const size_t per_pos = (psi_slots + p.S) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
   const int64_t cap = p.workspace_bytes ? p.workspace_bytes : kDefaultWorkspace;
   int64_t chunk = cap / (int64_t)per_pos;
   if (chunk < 1) {
@@ -345,7 +353,7 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   rc = PTYCHO_OK;
   if (!rc) rc = dev_alloc(&pl->d_tw, M, "twiddles");
   if (!rc) rc = dev_alloc(&pl->d_hs, M, "propagator");
-  if (!rc) rc = dev_alloc(&pl->ws_psi, (size_t)pl->chunk * (p.S - 1) * MM, "wave workspace");
+  if (!rc) rc = dev_alloc(&pl->ws_psi, (size_t)pl->chunk * psi_slots * MM, "wave workspace");
   if (!rc) rc = dev_alloc(&pl->ws_gphi, (size_t)pl->chunk * p.S * MM, "adjoint workspace");
   if (!rc) rc = dev_alloc(&pl->ws_gp, (size_t)pl->chunk * MM, "probe-gradient workspace");
   if (!rc) rc = dev_alloc(&pl->gp_part, (size_t)kProbeSplit * MM, "probe-gradient partials");
@@ -516,6 +524,32 @@ int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptyc
     TIMED(K_OTHER, 1, launch_axpy(P, plan->g_probe, P, -t * alpha_probe, nP, st));
   }
   if (t_out) *t_out = t;
+  return PTYCHO_OK;
+}
+
+int ptycho_potential_to_transmission(const float* V, ptycho_c64* obj, int64_t n, double sigma, void* stream) {
+  g_last_error.clear();
+  if (n < 0 || !std::isfinite(sigma)) return fail(PTYCHO_ERR_ARG, "n must be >= 0 and sigma finite");
+  if (n == 0) return PTYCHO_OK;
+  int rc;
+  if ((rc = check_array(obj, "obj", true))) return rc;
+  if (!is_device_ptr(V) || !aligned(V, 4)) return fail(PTYCHO_ERR_ARG, "V must be a 4-byte aligned device pointer");
+  CUDA_TRY(launch_potential_to_transmission(V, reinterpret_cast<float2*>(obj), sigma, (size_t)n,
+                                            static_cast<cudaStream_t>(stream)));
+  return PTYCHO_OK;
+}
+
+int ptycho_potential_grad(const ptycho_c64* obj, const ptycho_c64* grad_obj, float* grad_V, int64_t n,
+                          double sigma, void* stream) {
+  g_last_error.clear();
+  if (n < 0 || !std::isfinite(sigma)) return fail(PTYCHO_ERR_ARG, "n must be >= 0 and sigma finite");
+  if (n == 0) return PTYCHO_OK;
+  int rc;
+  if ((rc = check_array(obj, "obj", true)) || (rc = check_array(grad_obj, "grad_obj", true))) return rc;
+  if (!is_device_ptr(grad_V) || !aligned(grad_V, 4))
+    return fail(PTYCHO_ERR_ARG, "grad_V must be a 4-byte aligned device pointer");
+  CUDA_TRY(launch_potential_grad(reinterpret_cast<const float2*>(obj), reinterpret_cast<const float2*>(grad_obj),
+                                 grad_V, sigma, (size_t)n, static_cast<cudaStream_t>(stream)));
   return PTYCHO_OK;
 }
 

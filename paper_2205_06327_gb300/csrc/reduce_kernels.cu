@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kAccThreads, 2) k_accum_obj_grad(const AccumAr
   const int npix = th * tw;
   const size_t MM = (size_t)M * M;
   const float2* gphi_s = a.ws_gphi + (size_t)s * a.ws_n * MM;
-  const float2* psi_s = s > 0 ? a.ws_psi + (size_t)(s - 1) * a.ws_n * MM : nullptr;
+  const float2* psi_s = s > 0 && !a.patch_mode ? a.ws_psi + (size_t)(s - 1) * a.ws_n * MM : nullptr;
   float2* out = a.grad_obj + (size_t)s * a.H * a.W;
   constexpr int GROUP = kAccPPT * kAccThreads;
 
@@ -95,23 +95,43 @@ __global__ void __launch_bounds__(kAccThreads, 2) k_accum_obj_grad(const AccumAr
           const int i = lidx[live ? j : 0];
           const int oy0 = ty0 - rr.x, ox0 = tx0 - rr.y;
           const float2* gp = gphi_s + (size_t)i * MM;
-          const float2* pp = s > 0 ? psi_s + (size_t)i * MM : a.probe;
+          const float2* pp = s > 0 && !a.patch_mode ? psi_s + (size_t)i * MM : a.probe;
+          if (a.patch_mode) {  // finished patches conj(psi) g_phi
 #pragma unroll
-          for (int k = 0; k < kAccPPT; ++k) {
-            const int oy = oy0 + rowk[k], ox = ox0 + colk[k];
-            const bool in = live && (unsigned)oy < (unsigned)M && (unsigned)ox < (unsigned)M;
-            const int idx = in ? oy * M + ox : 0;
-            pv[u][k] = in ? (s > 0 ? ld_stream(pp + idx) : __ldg(pp + idx)) : make_float2(0.f, 0.f);
-            gv[u][k] = in ? ld_stream(gp + idx) : make_float2(0.f, 0.f);
+            for (int k = 0; k < kAccPPT; ++k) {
+              const int oy = oy0 + rowk[k], ox = ox0 + colk[k];
+              const bool in = live && (unsigned)oy < (unsigned)M && (unsigned)ox < (unsigned)M;
+              pv[u][k] = in ? ld_stream(gp + oy * M + ox) : make_float2(0.f, 0.f);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < kAccPPT; ++k) {
+              const int oy = oy0 + rowk[k], ox = ox0 + colk[k];
+              const bool in = live && (unsigned)oy < (unsigned)M && (unsigned)ox < (unsigned)M;
+              const int idx = in ? oy * M + ox : 0;
+              pv[u][k] = in ? (s > 0 ? ld_stream(pp + idx) : __ldg(pp + idx)) : make_float2(0.f, 0.f);
+              gv[u][k] = in ? ld_stream(gp + idx) : make_float2(0.f, 0.f);
+            }
           }
         }
+        if (a.patch_mode) {
 #pragma unroll
-        for (int u = 0; u < kAccUnroll; ++u) {
+          for (int u = 0; u < kAccUnroll; ++u) {
 #pragma unroll
-          for (int k = 0; k < kAccPPT; ++k) {
-            const float2 p = pv[u][k], g = gv[u][k];
-            acc[k].x = fmaf(p.x, g.x, fmaf(p.y, g.y, acc[k].x));
-            acc[k].y = fmaf(p.x, g.y, fmaf(-p.y, g.x, acc[k].y));
+            for (int k = 0; k < kAccPPT; ++k) {
+              acc[k].x += pv[u][k].x;
+              acc[k].y += pv[u][k].y;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < kAccUnroll; ++u) {
+#pragma unroll
+            for (int k = 0; k < kAccPPT; ++k) {
+              const float2 p = pv[u][k], g = gv[u][k];
+              acc[k].x = fmaf(p.x, g.x, fmaf(p.y, g.y, acc[k].x));
+              acc[k].y = fmaf(p.x, g.y, fmaf(-p.y, g.x, acc[k].y));
+            }
           }
         }
       }
@@ -203,6 +223,25 @@ __global__ void k_norm2_part(const float2* __restrict__ x, size_t n, double* par
   if (t == 0) part[blockIdx.x] = sh[0];
 }
 
+// O = exp(i sigma V) for a real potential V (Sec. II-B's unknown).
+__global__ void k_potential_to_transmission(const float* __restrict__ V, float2* __restrict__ O, float sigma,
+                                            size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float sn, cs;
+    sincosf(sigma * V[i], &sn, &cs);
+    O[i] = make_float2(cs, sn);
+  }
+}
+
+// dF/dV = sigma * Im(conj(O) dF/dO) for O = exp(i sigma V), V real.
+__global__ void k_potential_grad(const float2* __restrict__ O, const float2* __restrict__ g, float* __restrict__ gV,
+                                 float sigma, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 o = O[i], d = g[i];
+    gV[i] = sigma * fmaf(o.x, d.y, -o.y * d.x);
+  }
+}
+
 __global__ void k_check_positions(const int2* __restrict__ pos, int n, int M, int H, int W, int* status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -243,6 +282,21 @@ cudaError_t launch_norm2(const float2* x, size_t n, double* part, int n_part, do
                          cudaStream_t st) {
   k_norm2_part<<<n_part, 256, 0, st>>>(x, n, part);
   k_loss_accum<<<1, 256, 0, st>>>(part, n_part, out + slot, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_potential_to_transmission(const float* V, float2* O, double sigma, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + 255) / 256;
+  k_potential_to_transmission<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(V, O, (float)sigma, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_potential_grad(const float2* O, const float2* g, float* gV, double sigma, size_t n,
+                                  cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + 255) / 256;
+  k_potential_grad<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(O, g, gV, (float)sigma, n);
   return cudaGetLastError();
 }
 

@@ -288,3 +288,64 @@ def test_autograd_function(dev):
     assert abs(L.item() - Lr) <= 1e-5 * Lr
     assert rel_l2(O.grad.cpu().numpy(), 2 * gO) <= TOL_FP32
     assert rel_l2(P.grad.cpu().numpy(), 2 * gP) <= TOL_FP32
+
+
+def test_potential_parameterisation(dev):
+    """O = exp(i sigma V) and dF/dV = sigma Im(conj(O) dF/dO) against the oracle, and
+    the autograd path over V against FP64 finite differences of the oracle loss."""
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300.autograd import ptycho_loss_potential
+    wl = synth.workload_random(64, 3, 3, 3, 8, seed=31)
+    sigma = 0.7
+    V = (wl.potential / sigma).astype(np.float32)
+    I = measurements(wl)
+    Vd = to_dev(V, torch.float32, dev)
+    O = api.potential_to_transmission(Vd, sigma)
+    O_ref = np.exp(1j * sigma * V.astype(np.float64))
+    assert rel_l2(O.cpu().numpy(), O_ref) <= 1e-6
+    V0 = V + 0.05 * synth.rng(4).standard_normal(V.shape).astype(np.float32)
+    plan = _plan(wl, dev)
+    Vt = to_dev(V0, torch.float32, dev).requires_grad_(True)
+    L = ptycho_loss_potential(Vt, to_dev(wl.probe, torch.complex64, dev), plan, to_dev(wl.pos, torch.int32, dev),
+                              to_dev(I, torch.float32, dev), sigma)
+    L.backward()
+    O0 = np.exp(1j * sigma * V0.astype(np.float64))
+    _, gO, _ = orc.loss_grad(c64(wl.probe), c64(O0), wl.pos, I.astype(np.float64), propagator(wl))
+    gV_ref = orc.potential_grad(c64(O0), gO, sigma)
+    assert rel_l2(Vt.grad.cpu().numpy(), gV_ref) <= TOL_FP32
+    d = synth.rng(5).standard_normal(V.shape)
+    e = 1e-4
+    fd = (orc.loss(c64(wl.probe), np.exp(1j * sigma * (V0 + e * d)), wl.pos, I.astype(np.float64), propagator(wl))
+          - orc.loss(c64(wl.probe), np.exp(1j * sigma * (V0 - e * d)), wl.pos, I.astype(np.float64),
+                     propagator(wl))) / (2 * e)
+    assert abs(float(np.sum(Vt.grad.cpu().numpy() * d)) - fd) <= 1e-4 * abs(fd)
+
+
+@pytest.mark.parametrize("M,S,L", [(64, 7, 3), (128, 5, 2), (64, 4, 1)])
+def test_recompute_mode_matches_store_all(dev, M, S, L):
+    """Checkpoint every L slices + per-segment recomputation: the loss is
+    bit-identical (same forward), the gradients agree with the store-all mode
+    to FP32 reassociation and with the oracle at the usual bar, and the
+    workspace per position shrinks."""
+    wl = synth.workload_random(M, S, 3, 4, 9, seed=40 + M + S, amp_jitter=0.1)
+    I = (measurements(wl) * 1.3).astype(np.float32)
+    obj = start_object(wl, "perturbed", 6)
+    ref = _run(wl, obj, I, dev)
+    rc = _check(wl, obj, I, dev, ckpt_every=L)
+    assert rc[0] == ref[0]
+    assert rel_l2(rc[1], ref[1]) <= 2e-6 and rel_l2(rc[2], ref[2]) <= 2e-6
+    p_all, p_rc = _plan(wl, dev), _plan(wl, dev, ckpt_every=L)
+    K = -(-S // L)
+    per = wl.M * wl.M * 8
+    assert p_all.workspace_bytes // wl.N == (2 * S - 1) * per + per + 8
+    assert p_rc.workspace_bytes // wl.N == (S + K - 1 + L + 1) * per + per + 8
+
+
+def test_recompute_mode_multislice_subset(dev):
+    wl = synth.workload_multislice()
+    wl.pos = wl.pos[::9]
+    I = measurements(wl, counts_seed=1002)
+    obj = start_object(wl, "perturbed", 2)
+    ref = _run(wl, obj, I, dev)
+    rc = _check(wl, obj, I, dev, fp32_floor=True, ckpt_every=4)
+    assert rc[0] == ref[0] and rel_l2(rc[1], ref[1]) <= 2e-6 and rel_l2(rc[2], ref[2]) <= 2e-6
