@@ -76,6 +76,22 @@ def chain_flops_per_position(M: int, S: int) -> float:
     return flops_per_position(M, S) - 8.0 * S * M * M
 
 
+def tensor_flops_per_position(M: int, S: int) -> float:
+    """Tensor-core flops of one position on the BF16-split path: 2S transforms
+    (S-1 propagations and the far field, forward and adjoint), each two
+    M x M x M complex products, each four real products of three BF16 terms."""
+    return 2 * S * 2 * 4 * 3 * 2.0 * M ** 3
+
+
+def peaks_tensor() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16_tflops": d.get("bf16_tflops", 1900.0), "src": "measured (cuBLAS bf16 burst)"}
+    return {"bf16_tflops": 1900.0, "src": "fallback"}
+
+
 def hbm_bytes_per_evaluation(wl) -> float:
     """Minimum bytes the method moves per evaluation: intensities once, object
     once, object gradient once, probe and its gradient."""
@@ -294,7 +310,8 @@ def run_gpu(args, world, rank, local, pool):
     tile = (0, 0)
     if args.config == 3:
         tile = ((wl.H + 7) // 8, (wl.W + 7) // 8)  # 8 x 8 tessellation of the gradient
-    plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=args.ckpt_every)
+    plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=args.ckpt_every,
+                    precision=args.precision)
     pos = torch.from_numpy(wl.pos).to(device)
     probe = torch.from_numpy(wl.probe.astype(np.complex64)).to(device)
     obj_true = torch.from_numpy(wl.obj.astype(np.complex64)).to(device)
@@ -347,11 +364,19 @@ def run_gpu(args, world, rank, local, pool):
     t_max = reduce_max(t_step, world, device)
     value = world * wl.N / t_max
 
-    # roofline of the dominant kernel (slice chain): FP32 ALU bound
+    # roofline of the dominant kernel (slice chain): FP32 ALU bound, or the
+    # tensor pipe for the BF16-split transforms
     chain_ms = tm["chain_ms"] / max(tm["chain_launches"], 1)
     chain_pos = tm["chain_positions"] / max(tm["chain_launches"], 1)
-    chain_flops = chain_flops_per_position(wl.M, wl.S) * chain_pos
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if args.precision != "fp32":
+        chain_flops = tensor_flops_per_position(wl.M, wl.S) * chain_pos
+        pk_t = peaks_tensor()
+        peak_tflops = pk_t["bf16_tflops"]
+        bound, peak_src = "tensor", pk_t["src"]
+    else:
+        chain_flops = chain_flops_per_position(wl.M, wl.S) * chain_pos
+        peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        bound, peak_src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
     achieved = chain_flops / (chain_ms / 1e3) / 1e12
     pk = peaks()
     accum_ms = tm["accum_ms"] / max(tm["accum_launches"], 1)
@@ -364,7 +389,8 @@ def run_gpu(args, world, rank, local, pool):
         hp = {k: v.cpu().pin_memory() for k, v in (("pos", pos), ("probe", probe), ("obj", obj), ("I", I))}
         h2d = sum(v.numel() * v.element_size() for v in hp.values())
         d2h = 8 + gO.numel() * 8 + gP.numel() * 8
-        eplan = api.Plan(geom, device, async_check=True, tile=tile)
+        eplan = api.Plan(geom, device, async_check=True, tile=tile, ckpt_every=args.ckpt_every,
+                         precision=args.precision)
         for _ in range(2):
             eplan.loss_grad(hp["pos"], hp["probe"], hp["obj"], hp["I"])
         torch.cuda.synchronize(device)
@@ -395,16 +421,18 @@ def run_gpu(args, world, rank, local, pool):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": wl.name, "positions": wl.N, "M": wl.M, "S": wl.S, "object": [wl.H, wl.W],
                    "tiles": list(tile) if tile != (0, 0) else [64, 64],
                    "l2": "flushed between timed steps (512 MiB write, outside the step events)",
                    "replicas": world, "wall_s": wall, "ckpt_every": args.ckpt_every,
                    "workspace_bytes": plan.workspace_bytes, "chunk": plan.chunk},
-        "roofline": {"bound": "alu", "kernel": "k_chain (slice chain, gradient mode)",
+        "roofline": {"bound": bound, "kernel": "k_chain (slice chain, gradient mode)"
+                     if args.precision == "fp32" else "k_chain_tc (BF16-split DFT products, gradient mode)",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
-                     "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "peak_src": peak_src,
                      "kernel_ms": chain_ms, "kernel_share": tm["chain_ms"] / max(sum(step_ms), 1e-9)},
         "hbm_kernels": {"accum_obj_grad": {"ms": accum_ms, "bytes": accum_bytes,
                                            "gbs": accum_bytes / (accum_ms / 1e3) / 1e9 if accum_ms else None,
@@ -434,6 +462,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=576)
     ap.add_argument("--positions", type=int, default=0, help="first N positions only (profiling cases)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "fp16x3"],
+                    help="bf16x3 / fp16x3: 2-D transforms as hi/lo split DFT products on the tensor cores")
     ap.add_argument("--ckpt-every", type=int, default=0,
                     help="recompute mode: keep a wave checkpoint every L slices (0 = keep all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

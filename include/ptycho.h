@@ -56,10 +56,20 @@ extern "C" {
 #define PTYCHO_ERR_POSITION   -2  /* a probe window lies outside the object */
 #define PTYCHO_ERR_CUDA       -3  /* a CUDA runtime call failed */
 #define PTYCHO_ERR_NOMEM      -4  /* workspace allocation failed */
-#define PTYCHO_ERR_TIMEOUT    -5  /* a bounded device-side wait gave up */
+#define PTYCHO_ERR_TIMEOUT    -5  /* a bounded device-side wait gave up (reported
+                                     by ptycho_plan_status after the stream syncs) */
 #define PTYCHO_ERR_UNSUPPORTED -6 /* probe window size not supported */
 
 #define PTYCHO_FP32    0   /* all bulk complex arithmetic in FP32 */
+#define PTYCHO_BF16X3  1   /* the 2-D transforms as DFT-matrix products on the
+                              tensor cores: operands split into BF16 hi + lo,
+                              three products per real product (hi*hi, hi*lo,
+                              lo*hi), FP32 accumulation; pointwise work FP32,
+                              loss FP64.  M = 128 only. */
+#define PTYCHO_FP16X3  2   /* the same with IEEE half hi + lo (22 significant
+                              bits instead of 16, same tensor rate); wave
+                              values must stay below 60000 in magnitude, else
+                              ptycho_plan_status reports PTYCHO_ERR_UNSUPPORTED. */
 
 /* Flags for ptycho_params.flags */
 #define PTYCHO_FLAG_ASYNC_CHECK 1  /* do not synchronise to validate positions
@@ -83,7 +93,7 @@ typedef struct {
   double lambda_A;    /* wavelength, Angstrom */
   double dz_A;        /* slice spacing, Angstrom */
   double pixel_A;     /* real-space pixel, Angstrom */
-  int32_t precision;  /* PTYCHO_FP32 */
+  int32_t precision;  /* PTYCHO_FP32, PTYCHO_BF16X3 or PTYCHO_FP16X3 */
   int32_t flags;      /* PTYCHO_FLAG_* */
   int64_t workspace_bytes; /* cap on the plan's workspace; 0 = 8 GiB.  Positions
                               are processed in chunks that fit the cap, so the

@@ -20,6 +20,8 @@ PTYCHO_ERR_NOMEM = -4
 PTYCHO_ERR_TIMEOUT = -5
 PTYCHO_ERR_UNSUPPORTED = -6
 PTYCHO_FP32 = 0
+PTYCHO_BF16X3 = 1
+PTYCHO_FP16X3 = 2
 PTYCHO_FLAG_ASYNC_CHECK = 1
 PTYCHO_FLAG_TIMING = 2
 

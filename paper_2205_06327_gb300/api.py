@@ -47,7 +47,7 @@ class Plan:
 
     def __init__(self, geom: Geometry, device: torch.device | int | str = "cuda",
                  workspace_bytes: int = 0, tile: tuple[int, int] = (0, 0), async_check: bool = False,
-                 timing: bool = False, ckpt_every: int = 0):
+                 timing: bool = False, ckpt_every: int = 0, precision: str = "fp32"):
         if not torch.cuda.is_available():
             raise RuntimeError("libptycho needs a CUDA device; there is no CPU fallback")
         self.lib = _lib.load()
@@ -58,7 +58,10 @@ class Plan:
         p = PtychoParams()
         p.M, p.S, p.H, p.W, p.N = geom.M, geom.S, geom.H, geom.W, geom.N
         p.lambda_A, p.dz_A, p.pixel_A = geom.lambda_A, geom.dz_A, geom.pixel_A
-        p.precision = _lib.PTYCHO_FP32
+        codes = {"fp32": _lib.PTYCHO_FP32, "bf16x3": _lib.PTYCHO_BF16X3, "fp16x3": _lib.PTYCHO_FP16X3}
+        if precision not in codes:
+            raise ValueError(f"precision must be one of {sorted(codes)}")
+        p.precision = codes[precision]
         p.flags = (_lib.PTYCHO_FLAG_ASYNC_CHECK if async_check else 0) | (_lib.PTYCHO_FLAG_TIMING if timing else 0)
         p.workspace_bytes = int(workspace_bytes)
         p.tile_h, p.tile_w = int(tile[0]), int(tile[1])

@@ -47,6 +47,12 @@ size_t chain_smem_bytes(int M);
 cudaError_t chain_prepare(int M);  // raise the dynamic shared-memory limit
 cudaError_t launch_chain(int M, ChainMode mode, const ChainArgs& a, cudaStream_t st);
 
+// chain_tc.cu (BF16 or F16 hi/lo split DFT products on tcgen05, M = 128)
+size_t chain_tc_smem_bytes();
+cudaError_t chain_tc_prepare();
+cudaError_t launch_chain_tc(ChainMode mode, const ChainArgs& a, const uint32_t* cplanes, bool f16,
+                            cudaStream_t st);
+
 // reduce_kernels.cu
 constexpr int kDefaultTile = 32;  // default owner tile of the object-gradient accumulation
 struct AccumArgs {

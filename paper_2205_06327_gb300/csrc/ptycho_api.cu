@@ -45,6 +45,120 @@ bool is_device_ptr(const void* p) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// Round to BF16 (nearest, ties to even) on the host.
+uint16_t host_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float host_bf16_to_float(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Round to IEEE half (nearest, ties to even) on the host, with subnormals.
+uint16_t host_f16(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint32_t sign = (x >> 16) & 0x8000u;
+  const uint32_t fexp = (x >> 23) & 0xFFu;
+  uint32_t mant = x & 0x7FFFFFu;
+  if (fexp == 0xFFu) return (uint16_t)(sign | 0x7C00u | (mant ? 0x200u : 0u));
+  int exp = (int)fexp - 127 + 15;
+  if (exp >= 31) return (uint16_t)(sign | 0x7C00u);
+  if (exp <= 0) {
+    const int shift = 14 - exp;  // 24-bit significand -> subnormal units of 2^-24
+    if (shift > 24) return (uint16_t)sign;
+    mant |= 0x800000u;
+    uint32_t q = mant >> shift;
+    const uint32_t rem = mant & ((1u << shift) - 1u), halfway = 1u << (shift - 1);
+    if (rem > halfway || (rem == halfway && (q & 1u))) ++q;
+    return (uint16_t)(sign | q);
+  }
+  uint32_t q = mant >> 13;
+  const uint32_t rem = mant & 0x1FFFu;
+  if (rem > 0x1000u || (rem == 0x1000u && (q & 1u))) {
+    if (++q == 0x400u) {
+      q = 0;
+      if (++exp >= 31) return (uint16_t)(sign | 0x7C00u);
+    }
+  }
+  return (uint16_t)(sign | ((uint32_t)exp << 10) | q);
+}
+float host_f16_to_float(uint16_t h) {
+  const uint32_t sign = (uint32_t)(h & 0x8000u) << 16;
+  const int e = (h >> 10) & 0x1F;
+  const uint32_t m = h & 0x3FFu;
+  float v;
+  if (e == 0) v = std::ldexp((float)m, -24);
+  else if (e == 31) v = m ? NAN : INFINITY;
+  else v = std::ldexp((float)(m | 0x400u), e - 25);
+  return sign ? -v : v;
+}
+
+// Tensor-core operand planes of the two transform matrices, computed in FP64:
+//   K[m][n] = (1/M) sum_k h1(k) exp(+2 pi i k (m - n) / M)   (propagator, separable factor)
+//   F[m][n] = exp(-2 pi i m n / M) / sqrt(M)                  (orthonormal DFT)
+// Each entry is split into BF16 hi + lo for the real and imaginary parts;
+// row m of a plane is 64 words, element 2c in the low half of word c.
+std::vector<uint32_t> build_tc_planes(const ptycho_params& p, bool f16) {
+  const int M = p.M;
+  std::vector<uint32_t> out((size_t)2 * 4 * M * (M / 2));
+  std::vector<double> h1r(M), h1i(M);
+  for (int k = 0; k < M; ++k) {
+    const double f = (double)(k < M / 2 ? k : k - M) / ((double)M * p.pixel_A);
+    const double ph = -M_PI * p.lambda_A * p.dz_A * f * f;
+    h1r[k] = std::cos(ph);
+    h1i[k] = std::sin(ph);
+  }
+  const double two_pi = 6.283185307179586476925287;
+  for (int which = 0; which < 2; ++which) {
+    std::vector<double> cr((size_t)M * M), ci((size_t)M * M);
+    for (int m = 0; m < M; ++m)
+      for (int n = 0; n < M; ++n) {
+        if (which == 0) {
+          double sr = 0.0, si = 0.0;
+          for (int k = 0; k < M; ++k) {
+            const double a = two_pi * (double)k * (double)(m - n) / (double)M;
+            const double c = std::cos(a), s = std::sin(a);
+            sr += h1r[k] * c - h1i[k] * s;
+            si += h1r[k] * s + h1i[k] * c;
+          }
+          cr[(size_t)m * M + n] = sr / M;
+          ci[(size_t)m * M + n] = si / M;
+        } else {
+          const double a = -two_pi * (double)(((long long)m * n) % M) / (double)M;
+          cr[(size_t)m * M + n] = std::cos(a) / std::sqrt((double)M);
+          ci[(size_t)m * M + n] = std::sin(a) / std::sqrt((double)M);
+        }
+      }
+    for (int part = 0; part < 2; ++part) {
+      const std::vector<double>& src = part == 0 ? cr : ci;
+      for (int m = 0; m < M; ++m)
+        for (int c = 0; c < M / 2; ++c) {
+          uint16_t hi[2], lo[2];
+          for (int e = 0; e < 2; ++e) {
+            const float x = (float)src[(size_t)m * M + 2 * c + e];
+            if (f16) {
+              hi[e] = host_f16(x);
+              lo[e] = host_f16(x - host_f16_to_float(hi[e]));
+            } else {
+              hi[e] = host_bf16(x);
+              lo[e] = host_bf16(x - host_bf16_to_float(hi[e]));
+            }
+          }
+          const size_t base = ((size_t)which * 4 * M + (size_t)m) * (M / 2) + c;
+          out[base + (size_t)(2 * part) * M * (M / 2)] = (uint32_t)hi[1] << 16 | hi[0];
+          out[base + (size_t)(2 * part + 1) * M * (M / 2)] = (uint32_t)lo[1] << 16 | lo[0];
+        }
+    }
+  }
+  return out;
+}
+
 constexpr int64_t kDefaultWorkspace = 8ll << 30;
 constexpr int kProbeSplit = 32;
 constexpr int kNormParts = 512;
@@ -73,6 +187,7 @@ struct ptycho_plan_s {
   // gradient-descent step buffers (allocated on first use)
   float2* g_obj = nullptr;
   float2* g_probe = nullptr;
+  uint32_t* d_cplanes = nullptr;  // BF16X3: [K, F][re_hi, re_lo, im_hi, im_lo][128][64] packed BF16 pairs
   // kernel timing: event pairs per kernel family, launch counters
   struct Mark {
     int kind;
@@ -103,6 +218,7 @@ void free_plan(ptycho_plan pl) {
   cudaFree(pl->d_status);
   cudaFree(pl->g_obj);
   cudaFree(pl->g_probe);
+  cudaFree(pl->d_cplanes);
   if (pl->h_pos) cudaFreeHost(pl->h_pos);
   if (pl->h_scal) cudaFreeHost(pl->h_scal);
   delete pl;
@@ -128,7 +244,12 @@ int validate_params(const ptycho_params& p) {
   if (p.S < 1) return fail(PTYCHO_ERR_ARG, "S must be >= 1");
   if (p.H < p.M || p.W < p.M) return fail(PTYCHO_ERR_ARG, "object must be at least M x M");
   if (p.N < 0) return fail(PTYCHO_ERR_ARG, "N must be >= 0");
-  if (p.precision != PTYCHO_FP32) return fail(PTYCHO_ERR_UNSUPPORTED, "precision must be PTYCHO_FP32");
+  if (p.precision != PTYCHO_FP32 && p.precision != PTYCHO_BF16X3 && p.precision != PTYCHO_FP16X3)
+    return fail(PTYCHO_ERR_UNSUPPORTED, "precision must be PTYCHO_FP32, PTYCHO_BF16X3 or PTYCHO_FP16X3");
+  if (p.precision != PTYCHO_FP32 && p.M != 128)
+    return fail(PTYCHO_ERR_UNSUPPORTED, "the tensor-core precisions support M = 128 only");
+  if (p.precision != PTYCHO_FP32 && p.ckpt_every > 0 && p.ckpt_every < p.S)
+    return fail(PTYCHO_ERR_UNSUPPORTED, "the tensor-core precisions do not support the recompute mode");
   if (!(p.pixel_A > 0) || !std::isfinite(p.lambda_A) || !std::isfinite(p.dz_A))
     return fail(PTYCHO_ERR_ARG, "bad propagator parameters");
   if (p.workspace_bytes < 0) return fail(PTYCHO_ERR_ARG, "workspace_bytes must be >= 0");
@@ -246,7 +367,10 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     a.pos_begin = c0;
     a.n_pos = n;
     const ChainMode mode = !want_grad ? MODE_LOSS : (pl->ckpt_L ? MODE_GRAD_RC : MODE_GRAD);
-    TIMED(K_CHAIN, 1, launch_chain(p.M, mode, a, st));
+    if (p.precision != PTYCHO_FP32)
+      TIMED(K_CHAIN, 1, launch_chain_tc(mode, a, pl->d_cplanes, p.precision == PTYCHO_FP16X3, st));
+    else
+      TIMED(K_CHAIN, 1, launch_chain(p.M, mode, a, st));
     pl->tm.chain_positions += n;
     if (grad_obj) {
       AccumArgs g{};
@@ -311,7 +435,7 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
     return cuda_fail(e, "cudaGetDevice");
   }
   cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
-  if ((e = chain_prepare(p.M)) != cudaSuccess) {
+  if ((e = chain_prepare(p.M)) != cudaSuccess || (p.precision != PTYCHO_FP32 && (e = chain_tc_prepare()) != cudaSuccess)) {
     delete pl;
     return cuda_fail(e, "cudaFuncSetAttribute");
   }
@@ -331,7 +455,7 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
 
   // Workspace per position in flight (gradient mode).
   const size_t MM = (size_t)M * M;
-  pl->ckpt_L = (p.ckpt_every > 0 && p.ckpt_every < p.S) ? p.ckpt_every : 0;
+  pl->ckpt_L = (p.ckpt_every > 0 && p.ckpt_every < p.S && p.precision == PTYCHO_FP32) ? p.ckpt_every : 0;
   const int K = pl->ckpt_L ? (p.S + pl->ckpt_L - 1) / pl->ckpt_L : 0;
   const size_t psi_slots = pl->ckpt_L ? (size_t)(K - 1 + pl->ckpt_L + 1) : (size_t)(p.S - 1);
   const size_t per_pos = (psi_slots + p.S) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
@@ -361,9 +485,20 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   if (!rc) rc = dev_alloc(&pl->d_scal, 8, "scalars");
   if (!rc) rc = dev_alloc(&pl->norm_part, kNormParts, "norm partials");
   if (!rc) rc = dev_alloc(&pl->d_status, 1, "status");
+  std::vector<uint32_t> planes;
+  if (!rc && p.precision != PTYCHO_FP32) {
+    planes = build_tc_planes(p, p.precision == PTYCHO_FP16X3);
+    rc = dev_alloc(&pl->d_cplanes, planes.size(), "tensor-core operand planes");
+  }
   if (rc) {
     free_plan(pl);
     return rc;
+  }
+  if (!planes.empty() &&
+      (e = cudaMemcpy(pl->d_cplanes, planes.data(), planes.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) !=
+          cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "plane upload");
   }
   if (cudaMallocHost(&pl->h_pos, sizeof(int32_t) * 2 * (size_t)n) != cudaSuccess ||
       cudaMallocHost(&pl->h_scal, sizeof(double) * 8) != cudaSuccess) {
@@ -403,6 +538,8 @@ int ptycho_plan_status(ptycho_plan plan) {
   int h = 0;
   CUDA_TRY(cudaMemcpy(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(plan->d_status, 0, sizeof(int)));
+  if (h == PTYCHO_ERR_TIMEOUT) return fail(h, "a bounded tensor-core wait gave up on the device");
+  if (h == PTYCHO_ERR_UNSUPPORTED) return fail(h, "a wave value left the FP16 range (|x| >= 60000)");
   if (h) return fail(h, "a probe window outside the object was skipped on the device");
   return PTYCHO_OK;
 }
@@ -449,7 +586,10 @@ int ptycho_forward(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* pr
   for (int c0 = 0; c0 < p.N; c0 += step) {
     a.pos_begin = c0;
     a.n_pos = p.N - c0 < step ? p.N - c0 : step;
-    TIMED(K_CHAIN, 1, launch_chain(p.M, MODE_FORWARD, a, st));
+    if (p.precision != PTYCHO_FP32)
+      TIMED(K_CHAIN, 1, launch_chain_tc(MODE_FORWARD, a, pl->d_cplanes, p.precision == PTYCHO_FP16X3, st));
+    else
+      TIMED(K_CHAIN, 1, launch_chain(p.M, MODE_FORWARD, a, st));
     pl->tm.chain_positions += a.n_pos;
   }
   return PTYCHO_OK;

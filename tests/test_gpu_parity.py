@@ -349,3 +349,70 @@ def test_recompute_mode_multislice_subset(dev):
     ref = _run(wl, obj, I, dev)
     rc = _check(wl, obj, I, dev, fp32_floor=True, ckpt_every=4)
     assert rc[0] == ref[0] and rel_l2(rc[1], ref[1]) <= 2e-6 and rel_l2(rc[2], ref[2]) <= 2e-6
+
+
+# ------------------------------------------------ BF16 hi/lo split on tcgen05
+
+TOL_BF16X3 = 2e-4  # rel-L2 bound of the BF16-split path against the FP64 oracle
+
+
+# The BF16 hi + lo split represents each operand to about 2^-17; every
+# transform of the chain adds that error, which the amplitude residual then
+# amplifies, so the 2e-4 bar holds for one or two slices and the error grows
+# roughly 5e-5 per slice beyond (measured: S = 5 -> 2.4e-4 / 3.0e-4, S = 16 ->
+# 5.4e-4 / 1.1e-3 on gO / gP).  The FP16 split (22 bits) meets 2e-4 at 16 slices.
+BF16X3_DEEP_BAR = {5: 4e-4, 16: 2e-3}
+
+
+@pytest.mark.parametrize("S,ny,nx,step", [(1, 2, 3, 21), (2, 3, 2, 17), (5, 2, 2, 25)])
+def test_bf16x3_random_problems(dev, S, ny, nx, step):
+    wl = synth.workload_random(128, S, ny, nx, step, seed=60 + S, amp_jitter=0.15)
+    I = (measurements(wl) * 1.2).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 7), I, dev, tol=BF16X3_DEEP_BAR.get(S, TOL_BF16X3),
+           precision="bf16x3")
+
+
+def test_bf16x3_forward(dev):
+    wl = synth.workload_random(128, 4, 2, 2, 17, seed=61, amp_jitter=0.1)
+    Psi = orc.forward(c64(wl.probe), c64(wl.obj), wl.pos, propagator(wl))
+    plan = _plan(wl, dev, precision="bf16x3")
+    psi, inten = plan.forward(to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+                              to_dev(wl.obj, torch.complex64, dev), want_psi=True, want_intensity=True)
+    torch.cuda.synchronize()
+    e = rel_l2(psi.cpu().numpy(), Psi)
+    print(f"bf16x3 forward rel-L2 {e:.2e}")
+    assert e <= TOL_BF16X3
+    plan.status()
+
+
+def test_bf16x3_multislice_workload(dev):
+    """The 16-slice workload (every 4th position) at a perturbed start."""
+    wl = synth.workload_multislice()
+    wl.pos = wl.pos[::4]
+    I = measurements(wl, counts_seed=1002)
+    _check(wl, start_object(wl, "perturbed", 2), I, dev, tol=BF16X3_DEEP_BAR[16], precision="bf16x3")
+
+
+def test_bf16x3_rejects_other_windows(dev):
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300._lib import PTYCHO_ERR_UNSUPPORTED, PtychoError
+    with pytest.raises(PtychoError) as e:
+        api.Plan(api.Geometry(64, 2, 200, 200, 4), dev, precision="bf16x3")
+    assert e.value.code == PTYCHO_ERR_UNSUPPORTED
+
+
+TOL_FP16X3 = 2e-4
+
+
+@pytest.mark.parametrize("S", [1, 5])
+def test_fp16x3_random_problems(dev, S):
+    wl = synth.workload_random(128, S, 2, 3, 19, seed=70 + S, amp_jitter=0.15)
+    I = (measurements(wl) * 1.2).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 7), I, dev, tol=TOL_FP16X3, precision="fp16x3")
+
+
+def test_fp16x3_multislice_workload(dev):
+    wl = synth.workload_multislice()
+    wl.pos = wl.pos[::4]
+    I = measurements(wl, counts_seed=1002)
+    _check(wl, start_object(wl, "perturbed", 2), I, dev, tol=TOL_FP16X3, precision="fp16x3")
