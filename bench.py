@@ -249,6 +249,34 @@ def barrier(world: int, device=None):
 # arms
 # --------------------------------------------------------------------------
 
+CHAIN_SOURCES = {"fp32": ("chain_kernels.cu", "fft2d.cuh"), "bf16x3": ("chain_tc.cu", "tc_bf16.cuh"),
+                 "fp16x3": ("chain_tc.cu", "tc_bf16.cuh")}
+
+
+def chain_source_hash(precision: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in CHAIN_SOURCES[precision]:
+        with open(os.path.join(ROOT, "paper_2205_06327_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic_per_position(precision: str, M: int, S: int):
+    """DRAM bytes per position of the chain kernel from the committed ncu capture
+    (profiles/traffic.json), or None if the kernel changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"{precision}_M{M}_S{S}")
+    if not e or e.get("source_hash") != chain_source_hash(precision):
+        return None
+    return float(e["dram_bytes_per_position"])
+
+
 def peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -378,6 +406,8 @@ def run_gpu(args, world, rank, local, pool):
         peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         bound, peak_src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
     achieved = chain_flops / (chain_ms / 1e3) / 1e12
+    tpp = measured_traffic_per_position(args.precision, wl.M, wl.S)
+    traffic = tpp * chain_pos if tpp is not None else None
     pk = peaks()
     accum_ms = tm["accum_ms"] / max(tm["accum_launches"], 1)
     accum_bytes = 2.0 * wl.N * wl.S * wl.M * wl.M * 8 + wl.S * wl.H * wl.W * 8
@@ -424,14 +454,14 @@ def run_gpu(args, world, rank, local, pool):
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": wl.name, "positions": wl.N, "M": wl.M, "S": wl.S, "object": [wl.H, wl.W],
-                   "tiles": list(tile) if tile != (0, 0) else [64, 64],
+                   "tiles": list(tile) if tile != (0, 0) else [32, 32],
                    "l2": "flushed between timed steps (512 MiB write, outside the step events)",
                    "replicas": world, "wall_s": wall, "ckpt_every": args.ckpt_every,
                    "workspace_bytes": plan.workspace_bytes, "chunk": plan.chunk},
         "roofline": {"bound": bound, "kernel": "k_chain (slice chain, gradient mode)"
-                     if args.precision == "fp32" else "k_chain_tc (BF16-split DFT products, gradient mode)",
+                     if args.precision == "fp32" else "k_chain_tc (split DFT products, gradient mode)",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops, "traffic": traffic,
                      "peak_src": peak_src,
                      "kernel_ms": chain_ms, "kernel_share": tm["chain_ms"] / max(sum(step_ms), 1e-9)},
         "hbm_kernels": {"accum_obj_grad": {"ms": accum_ms, "bytes": accum_bytes,
@@ -453,12 +483,95 @@ def run_gpu(args, world, rank, local, pool):
     return 0
 
 
+def run_multi(args, world, rank, local):
+    """Batched uneven reconstructions: the 32 seeded problem shapes, each
+    advanced by fixed-step gradient descent, all problems of one iteration in a
+    single captured CUDA graph; the accumulation tile is tuned per window size."""
+    import torch
+
+    from paper_2205_06327_gb300 import api, autotune, synth
+    from paper_2205_06327_gb300.multi import MultiProblem, Problem, supported
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    shapes = synth.multi_problem_shapes()
+    probs, skipped = [], []
+    for p, (M, S, ny, nx, step) in enumerate(shapes):
+        if not supported(M, args.precision):
+            skipped.append(M)
+            continue
+        wl = synth.workload_random(M, S, ny, nx, step, seed=synth.MULTI_SEED_BASE + p)
+        g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+        pos = torch.from_numpy(wl.pos).to(device)
+        probe = torch.from_numpy(wl.probe.astype(np.complex64)).to(device)
+        truth = torch.from_numpy(wl.obj.astype(np.complex64)).to(device)
+        plan = api.Plan(g, device, async_check=True, precision=args.precision)
+        _, I = plan.forward(pos, probe, truth, want_psi=False, want_intensity=True)
+        plan.close()
+        obj = torch.from_numpy(start_object(wl, seed=p).astype(np.complex64)).to(device)
+        probs.append(Problem(g, pos, probe, obj, I * 1.05))
+        del truth
+    tiles = {}
+    for pr in probs:  # one tuning run per window size, on that class's first problem
+        if pr.geom.M not in tiles:
+            tiles[pr.geom.M] = autotune.tune_tile(pr.geom, pr.pos, pr.probe, pr.obj, pr.meas, device,
+                                                  precision=args.precision, use_cache=False)
+        pr.tile = tiles[pr.geom.M]
+    mp = MultiProblem(probs, device, precision=args.precision)
+    mp.capture(1e-3, 1e-6, warmup=args.warmup)
+    iters = args.iterations
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(device)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(local, None)
+    with clocks:
+        e0.record(stream)
+        mp.run(iters)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+    barrier(world, device)
+    mp.check_status()
+    t = e0.elapsed_time(e1) / 1e3
+    t_max = reduce_max(t, world, device)
+    per_it = mp.positions_per_iteration
+    value = world * per_it * iters / t_max
+    csum = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": iters, "warmup": args.warmup,
+        "ms_per_step": t_max / iters * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"{len(probs)} uneven problems (windows 64/128 of the 32 seeded shapes), "
+                               "one CUDA graph per gradient-descent iteration",
+                   "problems": len(probs), "skipped_windows": skipped,
+                   "positions_per_iteration": per_it, "iterations": iters,
+                   "tiles": {str(k): list(v) for k, v in tiles.items()},
+                   "l2": "inputs larger than L2 in aggregate; no flush between graph replays"},
+        "gpu_launches": None,
+        "clocks": {"sm_mhz": csum["sm_mhz"], "sm_max_mhz": csum["sm_max_mhz"], "reasons": csum["reasons"]},
+        "final_loss_sum": float(mp.loss.sum().item()),
+    }
+    mp.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5],
+                    help="workload: 1 single slice, 2 multislice (default), 3 PbTiO3-shaped, 5 batched uneven")
+    ap.add_argument("--iterations", type=int, default=50, help="gradient-descent iterations (workload 5)")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=576)
     ap.add_argument("--positions", type=int, default=0, help="first N positions only (profiling cases)")
@@ -474,6 +587,8 @@ def main(argv=None):
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.config == 5:
+        return run_multi(args, world, rank, local)
     pool = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # spawn the oracle's workers before the first CUDA call
