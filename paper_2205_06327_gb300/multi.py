@@ -1,0 +1,102 @@
+"""Several independent reconstructions advanced together, one CUDA graph per iteration.
+
+Each problem keeps its own plan (tables, workspace), device tensors and
+shape; one gradient-descent iteration of all problems -- for every problem the
+loss, both gradients (Eq. 1, Eq. 2) and the in-place update of O and P -- is
+captured once in a CUDA graph and replayed, so an iteration costs one graph
+launch however many problems and kernels it contains.  The workspace budget
+is shared: each plan gets ``workspace_bytes / n_problems`` and chunks its
+positions to fit.
+
+Windows supported by the kernels: 64 and 128 (FP32), 128 (tensor-core
+precisions).  ``supported(M)`` says which.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from .api import Geometry, Plan, _stream_handle
+
+SUPPORTED_WINDOWS = {"fp32": (64, 128), "bf16x3": (128,), "fp16x3": (128,)}
+
+
+def supported(M: int, precision: str = "fp32") -> bool:
+    return M in SUPPORTED_WINDOWS[precision]
+
+
+@dataclass
+class Problem:
+    geom: Geometry
+    pos: torch.Tensor     # int32 [N, 2] on the device
+    probe: torch.Tensor   # complex64 [M, M], updated in place
+    obj: torch.Tensor     # complex64 [S, H, W], updated in place
+    meas: torch.Tensor    # float32 [N, M, M]
+    tile: tuple[int, int] = (0, 0)
+
+
+class MultiProblem:
+    def __init__(self, problems: list[Problem], device, precision: str = "fp32",
+                 workspace_bytes: int = 32 << 30):
+        for p in problems:
+            if not supported(p.geom.M, precision):
+                raise ValueError(f"window {p.geom.M} is not supported with precision {precision}")
+        self.device = torch.device(device)
+        self.problems = problems
+        per = max(workspace_bytes // max(len(problems), 1), 1 << 20)
+        self.plans = [Plan(p.geom, self.device, workspace_bytes=per, tile=p.tile, async_check=True,
+                           precision=precision) for p in problems]
+        self.loss = torch.zeros(len(problems), dtype=torch.float64, device=self.device)
+        self.graph = None
+        self._alphas = None
+
+    @property
+    def positions_per_iteration(self) -> int:
+        return sum(p.geom.N for p in self.problems)
+
+    def step_all(self, alpha_obj: float, alpha_probe: float) -> None:
+        """One fixed-step gradient-descent iteration of every problem, eagerly."""
+        stream = _stream_handle(self.device)
+        t = C.c_double(0.0)
+        for i, (p, plan) in enumerate(zip(self.problems, self.plans)):
+            lp = self.loss.data_ptr() + 8 * i
+            _lib.check(plan.lib.ptycho_step(plan._h, p.pos.data_ptr(), p.probe.data_ptr(), p.obj.data_ptr(),
+                                            p.meas.data_ptr(), float(alpha_obj), float(alpha_probe), 0, lp,
+                                            C.byref(t), stream))
+
+    def capture(self, alpha_obj: float, alpha_probe: float, warmup: int = 1) -> None:
+        """Capture one iteration of all problems in a CUDA graph (after eager warm-up
+        iterations, which also allocate every workspace before capture)."""
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                self.step_all(alpha_obj, alpha_probe)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            self.step_all(alpha_obj, alpha_probe)
+        self.graph = g
+        self._alphas = (alpha_obj, alpha_probe)
+
+    def run(self, iterations: int) -> torch.Tensor:
+        """Replay the captured iteration; returns the loss of every problem before
+        the last iteration (float64 device tensor)."""
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        for _ in range(iterations):
+            self.graph.replay()
+        return self.loss
+
+    def check_status(self) -> None:
+        for plan in self.plans:
+            plan.status()
+
+    def close(self) -> None:
+        self.graph = None
+        for plan in self.plans:
+            plan.close()

@@ -1,0 +1,89 @@
+"""Several problems advanced together under one captured CUDA graph per
+iteration, and the measured accumulation-tile choice."""
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from paper_2205_06327_gb300 import synth
+from tests.helpers import c64, measurements, propagator, rel_l2, start_object, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda", 0)
+
+
+def _problems(dev, specs):
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300.multi import Problem
+    out, host = [], []
+    for k, (M, S, ny, nx, step) in enumerate(specs):
+        wl = synth.workload_random(M, S, ny, nx, step, seed=500 + k, amp_jitter=0.1)
+        I = (measurements(wl) * 1.1).astype(np.float32)
+        obj = start_object(wl, "perturbed", k)
+        g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+        out.append(Problem(g, to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+                           to_dev(obj, torch.complex64, dev), to_dev(I, torch.float32, dev)))
+        host.append((wl, obj, I))
+    return out, host
+
+
+SPECS = [(64, 2, 3, 3, 9), (128, 3, 2, 2, 21), (64, 1, 4, 2, 11), (128, 1, 2, 3, 19)]
+
+
+def test_graph_replay_matches_eager_and_oracle(dev):
+    from paper_2205_06327_gb300.multi import MultiProblem
+    a_o, a_p = 2e-3, 1e-5
+    probs, host = _problems(dev, SPECS)
+    eager, _ = _problems(dev, SPECS)
+    mp = MultiProblem(probs, dev)
+    me = MultiProblem(eager, dev)
+    mp.capture(a_o, a_p, warmup=1)   # warm-up = iteration 1, the capture itself runs nothing
+    me.step_all(a_o, a_p)
+    mp.run(2)                        # iterations 2 and 3
+    me.step_all(a_o, a_p)
+    me.step_all(a_o, a_p)
+    torch.cuda.synchronize()
+    mp.check_status()
+    for p, q in zip(probs, eager):   # graph replay == eager, bit for bit
+        assert torch.equal(p.obj, q.obj) and torch.equal(p.probe, q.probe)
+    assert torch.equal(mp.loss, me.loss)
+    for p, (wl, obj, I) in zip(probs, host):  # three FP64 oracle steps
+        P, O = c64(wl.probe), c64(obj)
+        h = propagator(wl)
+        for _ in range(3):
+            P, O, _, _ = orc.step(P, O, wl.pos, I.astype(np.float64), h, a_o, a_p)
+        assert rel_l2(p.obj.cpu().numpy(), O) <= 1e-6 and rel_l2(p.probe.cpu().numpy(), P) <= 1e-6
+    mp.close()
+    me.close()
+
+
+def test_unsupported_window_is_refused(dev):
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300.multi import MultiProblem, Problem, supported
+    assert supported(64) and supported(128) and not supported(96) and not supported(128 + 64)
+    g = api.Geometry(96, 1, 200, 200, 1)
+    z = torch.zeros(1, device=dev)
+    with pytest.raises(ValueError):
+        MultiProblem([Problem(g, z, z, z, z)], dev)
+
+
+def test_autotuner_picks_and_caches_a_tile(dev, tmp_path, monkeypatch):
+    from paper_2205_06327_gb300 import api, autotune
+    monkeypatch.setenv("PTYCHO_GB300_CACHE", str(tmp_path))
+    wl = synth.workload_random(64, 2, 4, 4, 6, seed=77)
+    I = measurements(wl)
+    g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    args = (to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+            to_dev(wl.obj, torch.complex64, dev), to_dev(I, torch.float32, dev))
+    tile = autotune.tune_tile(g, *args, device=dev, candidates=((16, 16), (32, 32)))
+    assert tile in ((16, 16), (32, 32))
+    assert autotune.tune_tile(g, *args, device=dev, candidates=()) == tile  # from the cache
+    assert (tmp_path / "autotune.json").exists()
