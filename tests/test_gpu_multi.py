@@ -87,3 +87,31 @@ def test_autotuner_picks_and_caches_a_tile(dev, tmp_path, monkeypatch):
     assert tile in ((16, 16), (32, 32))
     assert autotune.tune_tile(g, *args, device=dev, candidates=()) == tile  # from the cache
     assert (tmp_path / "autotune.json").exists()
+
+
+@pytest.mark.parametrize("batch", [1, 3, 7])
+def test_sequential_gd_matches_oracle_steps(dev, batch):
+    """Alg. 1's sequential update (batch = 1) and mini-batches: one epoch of
+    updates after every batch, against the same sequence of FP64 oracle steps."""
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300.sgd import SequentialGD
+    wl = synth.workload_random(64, 2, 2, 4, 10, seed=88, amp_jitter=0.1)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    obj0 = start_object(wl, "perturbed", 3)
+    g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    a_o, a_p = 5e-3, 2e-5
+    sgd = SequentialGD(g, batch, dev)
+    P = to_dev(wl.probe, torch.complex64, dev)
+    O = to_dev(obj0, torch.complex64, dev)
+    losses = sgd.epoch(to_dev(wl.pos, torch.int32, dev), P, O, to_dev(I, torch.float32, dev), a_o, a_p)
+    torch.cuda.synchronize()
+    Pr, Or = c64(wl.probe), c64(obj0)
+    h = propagator(wl)
+    ref_losses = []
+    for i0 in range(0, wl.N, batch):
+        sl = slice(i0, min(wl.N, i0 + batch))
+        Pr, Or, F0, _ = orc.step(Pr, Or, wl.pos[sl], I[sl].astype(np.float64), h, a_o, a_p)
+        ref_losses.append(F0)
+    assert np.allclose(losses.cpu().numpy(), ref_losses, rtol=1e-5)
+    assert rel_l2(O.cpu().numpy(), Or) <= 1e-6 and rel_l2(P.cpu().numpy(), Pr) <= 1e-6
+    sgd.close()
