@@ -545,8 +545,8 @@ def run_multi(args, world, rank, local):
         "ms_per_step": t_max / iters * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"{len(probs)} uneven problems (windows 64/128 of the 32 seeded shapes), "
-                               "one CUDA graph per gradient-descent iteration",
+        "config": {"workload": f"{len(probs)} uneven problems of the 32 seeded shapes (windows 64-256, "
+                               "1-24 slices), one CUDA graph per gradient-descent iteration",
                    "problems": len(probs), "skipped_windows": skipped,
                    "positions_per_iteration": per_it, "iterations": iters,
                    "tiles": {str(k): list(v) for k, v in tiles.items()},

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libptycho.so")
-SOURCES = ["chain_kernels.cu", "chain_tc.cu", "reduce_kernels.cu", "ptycho_api.cu", "noalloc.cu"]
+SOURCES = ["chain_kernels.cu", "chain_tc.cu", "chain_gm.cu", "reduce_kernels.cu", "ptycho_api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include")]

@@ -89,6 +89,8 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
       *a.status = PTYCHO_ERR_POSITION;
       if (MODE != MODE_FORWARD) a.loss_part[il] = 0.0;
     }
+    if (MODE == MODE_GRAD || MODE == MODE_GRAD_RC)
+      for (int k = t; k < M * M; k += C::T) a.ws_gp[(size_t)il * M * M + k] = make_float2(0.f, 0.f);
     return;
   }
   __syncthreads();

@@ -98,6 +98,8 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
       *a.status = PTYCHO_ERR_POSITION;
       if (MODE != MODE_FORWARD) a.loss_part[il] = 0.0;
     }
+    if (MODE == MODE_GRAD)
+      for (int k = t; k < TM * TM; k += blockDim.x) a.ws_gp[(size_t)il * TM * TM + k] = make_float2(0.f, 0.f);
     return;
   }
   if (w == 0) {

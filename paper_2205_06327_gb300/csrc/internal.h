@@ -53,6 +53,17 @@ cudaError_t chain_tc_prepare();
 cudaError_t launch_chain_tc(ChainMode mode, const ChainArgs& a, const uint32_t* cplanes, bool f16,
                             cudaStream_t st);
 
+// chain_gm.cu (any window M = 2^a 3^b, 8 <= M <= 4096, FP32)
+struct GmPlan {
+  int n;      // radix stages
+  int r[16];  // radices (4, 2, 3)
+};
+bool gm_supported(int M, GmPlan* plan);
+size_t gm_fft_smem_bytes(int M);
+cudaError_t gm_prepare(int M);
+cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int M, int* n_launches,
+                            cudaStream_t st);
+
 // reduce_kernels.cu
 constexpr int kDefaultTile = 32;  // default owner tile of the object-gradient accumulation
 struct AccumArgs {

@@ -177,6 +177,7 @@ struct ptycho_plan_s {
   float2* ws_psi = nullptr;   // [chunk][S-1][M][M]
   float2* ws_gphi = nullptr;  // [chunk][S][M][M]
   float2* ws_gp = nullptr;    // [chunk][M][M]
+  float2* wv = nullptr;       // generic-window path: [chunk][M][M] waves of the chunk
   float2* gp_part = nullptr;  // [kProbeSplit][M][M]
   double* loss_part = nullptr;  // [chunk]
   double* d_scal = nullptr;   // [8]: 0 loss, 1 |gO|^2, 2 |gP|^2, 3 trial loss
@@ -211,6 +212,7 @@ void free_plan(ptycho_plan pl) {
   cudaFree(pl->ws_psi);
   cudaFree(pl->ws_gphi);
   cudaFree(pl->ws_gp);
+  cudaFree(pl->wv);
   cudaFree(pl->gp_part);
   cudaFree(pl->loss_part);
   cudaFree(pl->d_scal);
@@ -239,8 +241,12 @@ int dev_alloc(T** p, size_t count, const char* what) {
   return PTYCHO_OK;
 }
 
+bool fused_window(int M) { return M == 64 || M == 128; }
+
 int validate_params(const ptycho_params& p) {
-  if (p.M != 64 && p.M != 128) return fail(PTYCHO_ERR_UNSUPPORTED, "probe window M must be 64 or 128");
+  if (!fused_window(p.M) && !(p.precision == PTYCHO_FP32 && gm_supported(p.M, nullptr)))
+    return fail(PTYCHO_ERR_UNSUPPORTED,
+                "probe window M must be 64 or 128, or (FP32) a product of powers of 2 and 3 in [8, 4096]");
   if (p.S < 1) return fail(PTYCHO_ERR_ARG, "S must be >= 1");
   if (p.H < p.M || p.W < p.M) return fail(PTYCHO_ERR_ARG, "object must be at least M x M");
   if (p.N < 0) return fail(PTYCHO_ERR_ARG, "N must be >= 0");
@@ -367,7 +373,12 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     a.pos_begin = c0;
     a.n_pos = n;
     const ChainMode mode = !want_grad ? MODE_LOSS : (pl->ckpt_L ? MODE_GRAD_RC : MODE_GRAD);
-    if (p.precision != PTYCHO_FP32)
+    int gm_launches = 0;
+    if (pl->wv) {
+      TIMED(K_CHAIN, 0, launch_chain_gm(mode, a, pl->wv, p.M, &gm_launches, st));
+      pl->tm.launches += gm_launches;
+      pl->tm.chain_launches += 1;
+    } else if (p.precision != PTYCHO_FP32)
       TIMED(K_CHAIN, 1, launch_chain_tc(mode, a, pl->d_cplanes, p.precision == PTYCHO_FP16X3, st));
     else
       TIMED(K_CHAIN, 1, launch_chain(p.M, mode, a, st));
@@ -435,7 +446,9 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
     return cuda_fail(e, "cudaGetDevice");
   }
   cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
-  if ((e = chain_prepare(p.M)) != cudaSuccess || (p.precision != PTYCHO_FP32 && (e = chain_tc_prepare()) != cudaSuccess)) {
+  if ((fused_window(p.M) && (e = chain_prepare(p.M)) != cudaSuccess) ||
+      (!fused_window(p.M) && (e = gm_prepare(p.M)) != cudaSuccess) ||
+      (p.precision != PTYCHO_FP32 && (e = chain_tc_prepare()) != cudaSuccess)) {
     delete pl;
     return cuda_fail(e, "cudaFuncSetAttribute");
   }
@@ -455,12 +468,22 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
 
   // Workspace per position in flight (gradient mode).
   const size_t MM = (size_t)M * M;
-  pl->ckpt_L = (p.ckpt_every > 0 && p.ckpt_every < p.S && p.precision == PTYCHO_FP32) ? p.ckpt_every : 0;
+  pl->ckpt_L = (p.ckpt_every > 0 && p.ckpt_every < p.S && p.precision == PTYCHO_FP32 && fused_window(M))
+                   ? p.ckpt_every
+                   : 0;
+  const bool gm = !fused_window(M);
   const int K = pl->ckpt_L ? (p.S + pl->ckpt_L - 1) / pl->ckpt_L : 0;
   const size_t psi_slots = pl->ckpt_L ? (size_t)(K - 1 + pl->ckpt_L + 1) : (size_t)(p.S - 1);
-  const size_t per_pos = (psi_slots + p.S) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
+  const size_t per_pos =
+      (psi_slots + p.S + (gm ? 1 : 0)) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
   const int64_t cap = p.workspace_bytes ? p.workspace_bytes : kDefaultWorkspace;
   int64_t chunk = cap / (int64_t)per_pos;
+  // generic-window path: keep the chunk's waves (streamed by every FFT pass)
+  // within about half of the L2
+  if (gm && chunk > 1) {
+    const int64_t l2cap = ((int64_t)64 << 20) / (int64_t)(MM * sizeof(float2));
+    if (chunk > l2cap) chunk = l2cap > 1 ? l2cap : 1;
+  }
   if (chunk < 1) {
     delete pl;
     return fail(PTYCHO_ERR_NOMEM, "workspace_bytes too small for one position");
@@ -480,6 +503,7 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   if (!rc) rc = dev_alloc(&pl->ws_psi, (size_t)pl->chunk * psi_slots * MM, "wave workspace");
   if (!rc) rc = dev_alloc(&pl->ws_gphi, (size_t)pl->chunk * p.S * MM, "adjoint workspace");
   if (!rc) rc = dev_alloc(&pl->ws_gp, (size_t)pl->chunk * MM, "probe-gradient workspace");
+  if (!rc && gm) rc = dev_alloc(&pl->wv, (size_t)pl->chunk * MM, "generic-window wave buffer");
   if (!rc) rc = dev_alloc(&pl->gp_part, (size_t)kProbeSplit * MM, "probe-gradient partials");
   if (!rc) rc = dev_alloc(&pl->loss_part, (size_t)pl->chunk, "loss partials");
   if (!rc) rc = dev_alloc(&pl->d_scal, 8, "scalars");
@@ -581,12 +605,20 @@ int ptycho_forward(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* pr
   ChainArgs a = base_args(plan, pos_yx, probe, obj, nullptr);
   a.psi_out = reinterpret_cast<float2*>(psi_out);
   a.int_out = intens_out;
-  const int step = 1 << 20;
+  // The register-resident and tensor-core kernels need no workspace in this
+  // mode; the generic-window path stages the chunk's waves in wv, which holds
+  // plan->chunk positions.
+  const int step = plan->wv ? plan->chunk : 1 << 20;
   ptycho_plan pl = plan;
   for (int c0 = 0; c0 < p.N; c0 += step) {
     a.pos_begin = c0;
     a.n_pos = p.N - c0 < step ? p.N - c0 : step;
-    if (p.precision != PTYCHO_FP32)
+    int gm_launches = 0;
+    if (pl->wv) {
+      TIMED(K_CHAIN, 0, launch_chain_gm(MODE_FORWARD, a, pl->wv, p.M, &gm_launches, st));
+      pl->tm.launches += gm_launches;
+      pl->tm.chain_launches += 1;
+    } else if (p.precision != PTYCHO_FP32)
       TIMED(K_CHAIN, 1, launch_chain_tc(MODE_FORWARD, a, pl->d_cplanes, p.precision == PTYCHO_FP16X3, st));
     else
       TIMED(K_CHAIN, 1, launch_chain(p.M, MODE_FORWARD, a, st));

@@ -8,8 +8,9 @@ launch however many problems and kernels it contains.  The workspace budget
 is shared: each plan gets ``workspace_bytes / n_problems`` and chunks its
 positions to fit.
 
-Windows supported by the kernels: 64 and 128 (FP32), 128 (tensor-core
-precisions).  ``supported(M)`` says which.
+Windows: 64 and 128 run the register-resident kernels; any other M = 2^a 3^b
+in [8, 4096] runs the generic batched-FFT path (FP32 only); the tensor-core
+precisions take M = 128.  ``supported(M)`` says which.
 """
 from __future__ import annotations
 
@@ -21,11 +22,18 @@ import torch
 from . import _lib
 from .api import Geometry, Plan, _stream_handle
 
-SUPPORTED_WINDOWS = {"fp32": (64, 128), "bf16x3": (128,), "fp16x3": (128,)}
+def _smooth(M: int) -> bool:
+    m = M
+    for p in (2, 3):
+        while m % p == 0:
+            m //= p
+    return m == 1
 
 
 def supported(M: int, precision: str = "fp32") -> bool:
-    return M in SUPPORTED_WINDOWS[precision]
+    if precision == "fp32":
+        return 8 <= M <= 4096 and _smooth(M)
+    return M == 128
 
 
 @dataclass
@@ -40,7 +48,7 @@ class Problem:
 
 class MultiProblem:
     def __init__(self, problems: list[Problem], device, precision: str = "fp32",
-                 workspace_bytes: int = 32 << 30):
+                 workspace_bytes: int = 96 << 30):
         for p in problems:
             if not supported(p.geom.M, precision):
                 raise ValueError(f"window {p.geom.M} is not supported with precision {precision}")

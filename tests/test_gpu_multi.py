@@ -68,8 +68,9 @@ def test_graph_replay_matches_eager_and_oracle(dev):
 def test_unsupported_window_is_refused(dev):
     from paper_2205_06327_gb300 import api
     from paper_2205_06327_gb300.multi import MultiProblem, Problem, supported
-    assert supported(64) and supported(128) and not supported(96) and not supported(128 + 64)
-    g = api.Geometry(96, 1, 200, 200, 1)
+    assert supported(64) and supported(128) and supported(96) and supported(192) and supported(256)
+    assert not supported(100) and supported(128, "bf16x3") and not supported(96, "fp16x3")
+    g = api.Geometry(100, 1, 200, 200, 1)
     z = torch.zeros(1, device=dev)
     with pytest.raises(ValueError):
         MultiProblem([Problem(g, z, z, z, z)], dev)

@@ -416,3 +416,66 @@ def test_fp16x3_multislice_workload(dev):
     wl.pos = wl.pos[::4]
     I = measurements(wl, counts_seed=1002)
     _check(wl, start_object(wl, "perturbed", 2), I, dev, tol=TOL_FP16X3, precision="fp16x3")
+
+
+# ------------------------------------------- generic windows (batched FFT path)
+
+@pytest.mark.parametrize("M,S,ny,nx,step", [(96, 1, 2, 3, 13), (96, 3, 2, 2, 17), (192, 2, 2, 2, 31),
+                                             (256, 3, 2, 2, 37), (48, 4, 3, 3, 7)])
+def test_generic_windows(dev, M, S, ny, nx, step):
+    wl = synth.workload_random(M, S, ny, nx, step, seed=90 + M + S, amp_jitter=0.15)
+    I = (measurements(wl) * 1.2).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 4), I, dev)
+
+
+def test_generic_window_forward_and_chunks(dev):
+    """Forward far field, and a workspace cap that splits the positions into chunks."""
+    wl = synth.workload_random(96, 2, 3, 4, 11, seed=97, amp_jitter=0.1)
+    Psi = orc.forward(c64(wl.probe), c64(wl.obj), wl.pos, propagator(wl))
+    plan = _plan(wl, dev)
+    psi, _ = plan.forward(to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+                          to_dev(wl.obj, torch.complex64, dev))
+    torch.cuda.synchronize()
+    assert rel_l2(psi.cpu().numpy(), Psi) <= TOL_FP32
+    I = (np.abs(Psi) ** 2 * 0.9).astype(np.float32)
+    per = (2 * wl.S - 1 + 1) * 96 * 96 * 8 + 96 * 96 * 8 + 8
+    ref = _run(wl, start_object(wl, "perturbed", 1), I, dev)
+    chunked = _run(wl, start_object(wl, "perturbed", 1), I, dev, workspace_bytes=5 * per)
+    assert abs(chunked[0] - ref[0]) <= 1e-12 * abs(ref[0])
+    assert rel_l2(chunked[1], ref[1]) <= 1e-6 and rel_l2(chunked[2], ref[2]) <= 1e-6
+
+
+def test_paper_scale_window_1024(dev):
+    """The paper's detector size (Table I: 1024^2 per position), two slices, two positions."""
+    wl = synth.workload_random(1024, 2, 1, 2, 200, seed=98, amp_jitter=0.1)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 2), I, dev)
+
+
+def test_generic_window_more_positions_than_a_chunk(dev):
+    """M = 256 keeps at most 128 waves per chunk (L2-sized): 130 positions take two
+    chunks in both the forward model and the gradient."""
+    wl = synth.workload_random(256, 1, 10, 13, 2, seed=99, amp_jitter=0.1)
+    assert wl.N == 130
+    Psi = orc.forward(c64(wl.probe), c64(wl.obj), wl.pos, propagator(wl))
+    plan = _plan(wl, dev)
+    assert plan.chunk < wl.N
+    _, inten = plan.forward(to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+                            to_dev(wl.obj, torch.complex64, dev), want_psi=False, want_intensity=True)
+    torch.cuda.synchronize()
+    assert rel_l2(inten.cpu().numpy(), np.abs(Psi) ** 2) <= TOL_FP32
+    I = (np.abs(Psi) ** 2 * 1.1).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 3), I, dev)
+
+
+def test_generic_windows_plans_coexist(dev):
+    """Plans for different generic windows created first, used afterwards (the
+    FFT kernels' shared-memory limit is shared by all plans)."""
+    wls = [synth.workload_random(M, 1, 2, 2, 9, seed=100 + M) for M in (256, 96)]
+    plans = [_plan(wl, dev) for wl in wls]
+    for wl, plan in zip(wls, plans):
+        I = (measurements(wl) * 1.2).astype(np.float32)
+        loss, _, _ = plan.loss_grad(to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
+                                    to_dev(wl.obj, torch.complex64, dev), to_dev(I, torch.float32, dev))
+        L = orc.loss(c64(wl.probe), c64(wl.obj), wl.pos, I.astype(np.float64), propagator(wl))
+        assert abs(loss.item() - L) <= TOL_FP32 * L
