@@ -26,7 +26,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _problem(M=12, S=2, ny=6, nx=7, step=3, seed=123):
+def _problem(M=16, S=2, ny=8, nx=8, step=2, seed=123):
     wl = synth.workload_random(M, S, ny, nx, step, seed=seed, amp_jitter=0.1)
     h = orc.fresnel_propagator(wl.M, wl.lambda_A, wl.dz_A, wl.pixel_A)
     I = orc.intensities(wl.probe, wl.obj, wl.pos, h) * 1.3
