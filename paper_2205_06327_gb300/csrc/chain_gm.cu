@@ -2,129 +2,145 @@
 // that the register-resident kernels do not cover (they take M = 64, 128).
 //
 // The chunk's positions advance through the multislice model (Sec. II-B)
-// together, slice by slice: their waves live in a global buffer wv[n][M][M],
-// every 2-D FFT is a batched pass over rows then a batched pass over columns
-// (mixed radix 4/2/3 Stockham autosort in shared memory, natural order, exact
-// inverse by conjugation), and pointwise kernels apply the transmission, the
-// Fresnel factor, the amplitude residual of Eq. 1 and their adjoints.  The
-// workspace it fills (entering waves, exit-wave gradients, probe-gradient
+// together, slice by slice: their waves live in a global buffer wv[n][M][M].
+// Every pass loads a block of rows or columns of one wave into shared memory,
+// transforms them with mixed-radix (8/4/2/3) Stockham stages in natural
+// order, and writes them back.  Because the Fresnel factor is separable, a
+// propagation is a row pass and a column pass, each running FFT, factor and
+// inverse on its lines; the transmission of a slice and its adjoint ride on
+// the row passes.  The amplitude residual of Eq. 1 is one pointwise kernel.
+// The workspace it fills (entering waves, exit-wave gradients, probe-gradient
 // parts, loss parts) has the layout of the register-resident kernels, so the
 // tiled reductions are shared.
 #include "../../include/ptycho.h"
+#include "fft2d.cuh"
 #include "internal.h"
 
 namespace ptycho {
 
 namespace {
 
-__device__ __forceinline__ float2 gcmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 gcmulc(float2 a, float2 b) {  // a * conj(b)
-  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
-}
-
-// Small DFTs (natural order), forward kernel exp(-2 pi i n k / R), inverse its conjugate.
-template <bool INV>
-__device__ __forceinline__ void dft_small(float2 (&x)[4], int R) {
-  if (R == 2) {
-    const float2 a = x[0], b = x[1];
-    x[0] = make_float2(a.x + b.x, a.y + b.y);
-    x[1] = make_float2(a.x - b.x, a.y - b.y);
-  } else if (R == 3) {
+// Small DFT of a register array in natural order, forward kernel
+// exp(-2 pi i n k / R), inverse its conjugate, unnormalised.
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2 (&x)[R]) {
+  if constexpr (R == 2) {
+    dft2(x[0], x[1]);
+  } else if constexpr (R == 3) {
     // X1 = t2 -+ i s3 (b - c), X2 = t2 +- i s3 (b - c), t2 = a - (b + c)/2
     const float s3 = 0.86602540378443864676f;
     const float2 a = x[0], b = x[1], c = x[2];
-    const float2 t1 = make_float2(b.x + c.x, b.y + c.y);
+    const float2 t1 = cadd(b, c);
     const float2 t2 = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
-    const float2 d = make_float2(s3 * (b.x - c.x), s3 * (b.y - c.y));  // s3 (b - c)
-    // -i d = (d.y, -d.x)
-    const float2 mid = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
-    x[0] = make_float2(a.x + t1.x, a.y + t1.y);
-    x[1] = make_float2(t2.x + mid.x, t2.y + mid.y);
-    x[2] = make_float2(t2.x - mid.x, t2.y - mid.y);
-  } else {  // R == 4
-    const float2 t0 = make_float2(x[0].x + x[2].x, x[0].y + x[2].y);
-    const float2 t1 = make_float2(x[0].x - x[2].x, x[0].y - x[2].y);
-    const float2 t2 = make_float2(x[1].x + x[3].x, x[1].y + x[3].y);
-    const float2 u = make_float2(x[1].x - x[3].x, x[1].y - x[3].y);
-    const float2 t3 = INV ? make_float2(-u.y, u.x) : make_float2(u.y, -u.x);  // -+ i (x1 - x3)
-    x[0] = make_float2(t0.x + t2.x, t0.y + t2.y);
-    x[2] = make_float2(t0.x - t2.x, t0.y - t2.y);
-    x[1] = make_float2(t1.x + t3.x, t1.y + t3.y);
-    x[3] = make_float2(t1.x - t3.x, t1.y - t3.y);
+    const float2 d = make_float2(s3 * (b.x - c.x), s3 * (b.y - c.y));
+    const float2 mid = mul_mi<INV>(d);
+    x[0] = cadd(a, t1);
+    x[1] = cadd(t2, mid);
+    x[2] = csub(t2, mid);
+  } else if constexpr (R == 4) {
+    dft4<INV>(x[0], x[1], x[2], x[3]);
+  } else {
+    static_assert(R == 8, "radix 2, 3, 4 or 8");
+    dft8<INV>(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7]);
   }
 }
 
-// Batched 1-D FFT of length M over L lines per block: rows (element stride 1)
-// or columns (element stride M) of the waves.  Stockham autosort: at a stage
-// of radix R after spans Ns, butterfly j takes x[j + t N/R], twiddles it by
-// w_{Ns R}^{t (j mod Ns)}, and writes y[(j / Ns) Ns R + j mod Ns + t Ns].
-template <bool INV>
-__global__ void __launch_bounds__(256) k_gm_fft(float2* __restrict__ data, int M, int L, int cols, GmPlan plan,
-                                                const float2* __restrict__ tw) {
-  extern __shared__ float2 gsm[];
-  float2* A = gsm;
-  float2* B = gsm + (size_t)L * M;
-  float2* T = B + (size_t)L * M;
-  const int t = threadIdx.x, nt = blockDim.x;
-  for (int k = t; k < M; k += nt) T[k] = tw[k];
-  const size_t MM = (size_t)M * M;
-  const int g0 = blockIdx.x * L;  // first line of this block (L divides M)
-  const size_t wave = (size_t)(g0 / M);
-  const int l0 = g0 % M;
-  float2* base = data + wave * MM;
-  const int n = L * M;
-  if (cols) {
-    for (int idx = t; idx < n; idx += nt) {
-      const int p = idx / L, li = idx % L;
-      A[li * M + p] = base[(size_t)p * M + l0 + li];
-    }
-  } else {
-    for (int idx = t; idx < n; idx += nt) A[idx] = base[(size_t)l0 * M + idx];
-  }
-  __syncthreads();
-  float2* src = A;
-  float2* dst = B;
-  int Ns = 1;
-  for (int st = 0; st < plan.n; ++st) {
-    const int R = plan.r[st];
-    const int nb = M / R;
-    const int tstep = M / (Ns * R);
-    for (int idx = t; idx < L * nb; idx += nt) {
-      const int li = idx / nb, j = idx % nb, k = j % Ns;
-      const float2* s = src + li * M;
-      float2 x[4];
+// One Stockham autosort stage of radix R on L lines of length M (line
+// stride LS in shared memory), after spans of Ns: butterfly j takes
+// x[j + q M/R], twiddles it by w_{Ns R}^{q (j mod Ns)} = w_M^{tstep q k}, and
+// writes y[(j - k) R + k + q Ns].  tstep q k < M, so the table needs no wrap.
+template <int R, bool INV>
+__device__ __forceinline__ void gm_stage(const float2* __restrict__ src, float2* __restrict__ dst, int M, int LS,
+                                         int L, int Ns, const float2* __restrict__ T, int t, int nt) {
+  const int nb = M / R;
+  const int tstep = M / (Ns * R);
+  for (int idx = t; idx < L * nb; idx += nt) {
+    const int li = idx / nb;
+    const int j = idx - li * nb;
+    const int k = j % Ns;
+    const float2* s = src + li * LS;
+    float2 x[R];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (q < R) x[q] = s[j + q * nb];
-      if (Ns > 1) {
+    for (int q = 0; q < R; ++q) x[q] = s[j + q * nb];
+    if (Ns > 1) {
 #pragma unroll
-        for (int q = 1; q < 4; ++q)
-          if (q < R) {
-            const float2 w = T[(tstep * q * k) % M];
-            x[q] = INV ? gcmulc(x[q], w) : gcmul(x[q], w);
-          }
+      for (int q = 1; q < R; ++q) {
+        const float2 w = T[tstep * q * k];
+        x[q] = INV ? cmulc(x[q], w) : cmul(x[q], w);
       }
-      dft_small<INV>(x, R);
-      float2* d = dst + li * M + (j / Ns) * Ns * R + k;
+    }
+    dft_r<R, INV>(x);
+    float2* d = dst + li * LS + (j - k) * R + k;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (q < R) d[q * Ns] = x[q];
-    }
-    __syncthreads();
-    float2* tmp = src;
-    src = dst;
-    dst = tmp;
-    Ns *= R;
+    for (int q = 0; q < R; ++q) d[q * Ns] = x[q];
   }
-  if (cols) {
-    for (int idx = t; idx < n; idx += nt) {
-      const int p = idx / L, li = idx % L;
-      base[(size_t)p * M + l0 + li] = src[li * M + p];
+}
+
+// Radix schedule of a window: as many 8s as divide it, then 4, 2, then 3s.
+__host__ __device__ constexpr int gm_radix_at(int M, int i) {
+  int m = M, k = 0;
+  const int order[4] = {8, 4, 2, 3};
+  for (int o = 0; o < 4; ++o)
+    while (m % order[o] == 0 && m > 1) {
+      if (k == i) return order[o];
+      m /= order[o];
+      ++k;
     }
+  return 0;
+}
+__host__ __device__ constexpr int gm_n_stages(int M) {
+  int n = 0;
+  while (gm_radix_at(M, n) != 0) ++n;
+  return n;
+}
+// Lines per block: the largest divisor of M with L M <= 4096.
+__host__ __device__ constexpr int gm_lines(int M) {
+  int best = 1;
+  for (int L = 1; L <= M && L * M <= 4096; ++L)
+    if (M % L == 0) best = L;
+  return best;
+}
+
+// Stages with everything known at compile time (window MC): index
+// arithmetic folds to multiplies and shifts.
+template <bool INV, int MC, int I, int NS>
+__device__ __forceinline__ float2* gm_stages_ct(float2* src, float2* dst, const float2* T, int t) {
+  if constexpr (I == gm_n_stages(MC)) {
+    return src;
   } else {
-    for (int idx = t; idx < n; idx += nt) base[(size_t)l0 * M + idx] = src[idx];
+    constexpr int R = gm_radix_at(MC, I);
+    gm_stage<R, INV>(src, dst, MC, MC + 1, gm_lines(MC), NS, T, t, 256);
+    __syncthreads();
+    return gm_stages_ct<INV, MC, I + 1, NS * R>(dst, src, T, t);
+  }
+}
+
+// All stages of one transform of the block's lines; returns the buffer that
+// holds the result.  MC = 0: the radix schedule is read from the plan.
+template <bool INV, int MC>
+__device__ __forceinline__ float2* gm_transform(float2* src, float2* dst, int M, int L, const GmPlan& plan,
+                                                const float2* T, int t) {
+  if constexpr (MC > 0) {
+    return gm_stages_ct<INV, MC, 0, 1>(src, dst, T, t);
+  } else {
+    int Ns = 1;
+    for (int st = 0; st < plan.n; ++st) {
+      const int R = plan.r[st];
+      if (R == 8)
+        gm_stage<8, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+      else if (R == 4)
+        gm_stage<4, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+      else if (R == 2)
+        gm_stage<2, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+      else
+        gm_stage<3, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+      __syncthreads();
+      float2* tmp = src;
+      src = dst;
+      dst = tmp;
+      Ns *= R;
+    }
+    return src;
   }
 }
 
@@ -154,54 +170,126 @@ __global__ void k_gm_init(const ChainArgs a, float2* __restrict__ wv, int M) {
   }
 }
 
-// Forward transmission of slice s: [store psi_s] then wv *= O_s[window] (+ dir).
-// Adjoint (ADJ): store g_phi_s, then wv = conj(O_s[window]) wv; at s = 0 the
-// result g_psi_0 goes to the probe-gradient workspace instead.
-template <bool ADJ>
-__global__ void k_gm_transmit(const ChainArgs a, float2* __restrict__ wv, int M, int s, int store) {
-  const size_t MM = (size_t)M * M, n = (size_t)a.n_pos * MM;
+// What one line pass does between loading and storing its lines.
+enum : int { GM_FFT = 0, GM_IFFT = 1, GM_PROP = 2, GM_PROP_CONJ = 3 };
+
+struct GmLineArgs {
+  int op;     // GM_*: transform, inverse, or 1-D propagation (FFT, x hs[k], IFFT)
+  int cols;   // 0: the lines are rows, 1: columns
+  int s;      // slice of a fused transmission (row passes only)
+  int pre;    // forward transmission on load: [store psi_s], times O_s[window]
+  int post;   // adjoint transmission on store: store g_phi_s, times conj(O_s[window])
+  int store;  // with pre: keep psi_s in the workspace
+};
+
+// One pass over L rows or columns of each wave.  The Fresnel factor is
+// separable, h(ky, kx) = h1(ky) h1(kx), so a propagation F^-1 h F is a 1-D
+// propagation of every row followed by one of every column: each pass keeps
+// its lines in shared memory through FFT, the factor hs[k] = h1(k)/M and the
+// inverse.  Row passes also apply the slice's transmission (Sec. II-B) on
+// load, or its adjoint on store, so a slice costs one row and one column
+// pass each way.
+//   forward transmission (pre):  [psi_s -> workspace], v = psi_s O_s[window] (+ step dir)
+//   adjoint transmission (post): g_phi_s -> workspace, v = conj(O_s[window]) g_phi_s,
+//                                at s = 0 into the probe-gradient workspace instead.
+// Skipped (out-of-range) windows carry zeros.
+template <int MC>
+__global__ void __launch_bounds__(256) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
+                                                 GmLineArgs g) {
+  if constexpr (MC > 0) M = MC;
+  const int L = MC > 0 ? gm_lines(MC) : gm_lines(M);
+  const int LS = M + 1;
+  extern __shared__ float2 gsm[];
+  float2* A = gsm;
+  float2* B = A + (size_t)L * LS;
+  float2* T = B + (size_t)L * LS;
+  float2* Hs = T + M;
+  const int t = threadIdx.x;
+  for (int k = t; k < M; k += 256) {
+    T[k] = a.tw[k];
+    Hs[k] = a.hs[k];
+  }
+  const size_t MM = (size_t)M * M;
+  const int g0 = blockIdx.x * L;  // first line of this block (L divides M)
+  const int il = g0 / M;
+  const int l0 = g0 - il * M;
+  float2* base = wv + (size_t)il * MM;
+  const int2 r = a.pos[a.pos_begin + il];
+  const bool ok = window_ok(r, M, a.H, a.W);
   const size_t HW = (size_t)a.H * a.W;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int il = (int)(idx / MM);
-    const int rem = (int)(idx % MM);
-    const int y = rem / M, x = rem % M;
-    const int2 r = a.pos[a.pos_begin + il];
-    float2 v = wv[idx];
-    if (!window_ok(r, M, a.H, a.W)) {  // skipped window: contributes nothing
-      wv[idx] = make_float2(0.f, 0.f);
-      if (ADJ && s == 0) __stcs(a.ws_gp + (size_t)il * MM + rem, make_float2(0.f, 0.f));
-      continue;
+  const int n = L * M;
+  if (g.cols) {
+    for (int idx = t; idx < n; idx += 256) {
+      const int p = idx / L, li = idx - p * L;
+      A[li * LS + p] = base[(size_t)p * M + l0 + li];
     }
-    const size_t oi = (size_t)s * HW + (size_t)(r.x + y) * a.W + (r.y + x);
-    if (!ADJ) {
-      if (store) __stcs(a.ws_psi + ((size_t)(s - 1) * a.ws_n + il) * MM + rem, v);
-      float2 o = a.obj[oi];
-      if (a.obj_dir) {
-        const float2 d = a.obj_dir[oi];
-        o.x = fmaf(a.obj_step, d.x, o.x);
-        o.y = fmaf(a.obj_step, d.y, o.y);
+  } else {
+    for (int idx = t; idx < n; idx += 256) {
+      const int li = idx / M, x = idx - li * M;
+      const size_t rem = (size_t)l0 * M + idx;
+      float2 v = base[rem];
+      if (g.pre) {
+        if (!ok) {
+          v = make_float2(0.f, 0.f);
+        } else {
+          if (g.store) __stcs(a.ws_psi + ((size_t)(g.s - 1) * a.ws_n + il) * MM + rem, v);
+          const size_t oi = (size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x);
+          float2 o = a.obj[oi];
+          if (a.obj_dir) {
+            const float2 d = a.obj_dir[oi];
+            o.x = fmaf(a.obj_step, d.x, o.x);
+            o.y = fmaf(a.obj_step, d.y, o.y);
+          }
+          v = cmul(v, o);
+        }
       }
-      wv[idx] = gcmul(v, o);
-    } else {
-      __stcs(a.ws_gphi + ((size_t)s * a.ws_n + il) * MM + rem, v);
-      const float2 g = gcmulc(v, a.obj[oi]);
-      if (s == 0)
-        __stcs(a.ws_gp + (size_t)il * MM + rem, g);
-      else
-        wv[idx] = g;
+      A[li * LS + x] = v;
     }
   }
-}
-
-// Spectrum times hs[ky] hs[kx] (the propagator with the 1/M^2 of an
-// unnormalised FFT pair folded in), or its conjugate.
-template <bool CONJ>
-__global__ void k_gm_prop(const ChainArgs a, float2* __restrict__ wv, int M) {
-  const size_t MM = (size_t)M * M, n = (size_t)a.n_pos * MM;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int rem = (int)(idx % MM);
-    const float2 h = gcmul(a.hs[rem / M], a.hs[rem % M]);
-    wv[idx] = CONJ ? gcmulc(wv[idx], h) : gcmul(wv[idx], h);
+  __syncthreads();
+  float2* out;
+  if (g.op == GM_FFT) {
+    out = gm_transform<false, MC>(A, B, M, L, plan, T, t);
+  } else if (g.op == GM_IFFT) {
+    out = gm_transform<true, MC>(A, B, M, L, plan, T, t);
+  } else {
+    float2* mid = gm_transform<false, MC>(A, B, M, L, plan, T, t);
+    const bool cj = g.op == GM_PROP_CONJ;
+    for (int idx = t; idx < n; idx += 256) {
+      const int li = idx / M, k = idx - li * M;
+      float2& z = mid[li * LS + k];
+      z = cj ? cmulc(z, Hs[k]) : cmul(z, Hs[k]);
+    }
+    __syncthreads();
+    out = gm_transform<true, MC>(mid, mid == A ? B : A, M, L, plan, T, t);
+  }
+  if (g.cols) {
+    for (int idx = t; idx < n; idx += 256) {
+      const int p = idx / L, li = idx - p * L;
+      base[(size_t)p * M + l0 + li] = out[li * LS + p];
+    }
+  } else {
+    for (int idx = t; idx < n; idx += 256) {
+      const int li = idx / M, x = idx - li * M;
+      const size_t rem = (size_t)l0 * M + idx;
+      const float2 v = out[li * LS + x];
+      if (!g.post) {
+        base[rem] = v;
+        continue;
+      }
+      if (!ok) {
+        base[rem] = make_float2(0.f, 0.f);
+        if (g.s == 0) __stcs(a.ws_gp + (size_t)il * MM + rem, make_float2(0.f, 0.f));
+        continue;
+      }
+      __stcs(a.ws_gphi + ((size_t)g.s * a.ws_n + il) * MM + rem, v);
+      const size_t oi = (size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x);
+      const float2 gv = cmulc(v, a.obj[oi]);
+      if (g.s == 0)
+        __stcs(a.ws_gp + (size_t)il * MM + rem, gv);
+      else
+        base[rem] = gv;
+    }
   }
 }
 
@@ -251,39 +339,44 @@ __global__ void __launch_bounds__(256) k_gm_residual(const ChainArgs a, float2* 
   }
 }
 
-int lines_per_block(int M) {
-  int best = 1;
-  for (int L = 1; L <= M && L * M <= 4096; ++L)
-    if (M % L == 0) best = L;
-  return best;
-}
-
 }  // namespace
 
 bool gm_supported(int M, GmPlan* plan) {
   if (M < 8 || M > 4096) return false;
   GmPlan p{};
-  int m = M;
-  while (m % 4 == 0) p.r[p.n++] = 4, m /= 4;
-  while (m % 2 == 0) p.r[p.n++] = 2, m /= 2;
-  while (m % 3 == 0) p.r[p.n++] = 3, m /= 3;
-  if (m != 1 || p.n > 16) return false;
+  p.n = gm_n_stages(M);
+  if (p.n > 16) return false;
+  int prod = 1;
+  for (int i = 0; i < p.n; ++i) prod *= (p.r[i] = gm_radix_at(M, i));
+  if (prod != M) return false;
   if (plan) *plan = p;
   return true;
 }
 
-size_t gm_fft_smem_bytes(int M) { return (2 * (size_t)lines_per_block(M) * M + M) * sizeof(float2); }
+size_t gm_fft_smem_bytes(int M) { return (2 * (size_t)gm_lines(M) * (M + 1) + 2 * (size_t)M) * sizeof(float2); }
+
+namespace {
+
+// Windows with a compile-time instance of the line pass; others take the
+// runtime radix schedule.
+template <int MC>
+cudaError_t gm_set_smem(int bytes) {
+  return cudaFuncSetAttribute(k_gm_line<MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace
 
 // The limit is an attribute of the kernel, shared by every plan in the
-// process: always raise it to what the largest supported window needs.
+// process: always raise it to what the largest window it serves needs.
 cudaError_t gm_prepare(int) {
   size_t most = 0;
   for (int M = 8; M <= 4096; ++M)
     if (gm_supported(M, nullptr) && gm_fft_smem_bytes(M) > most) most = gm_fft_smem_bytes(M);
-  const int bytes = (int)most;
-  cudaError_t e = cudaFuncSetAttribute(k_gm_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gm_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e;
+  if ((e = gm_set_smem<0>((int)most)) != cudaSuccess) return e;
+  if ((e = gm_set_smem<96>((int)gm_fft_smem_bytes(96))) != cudaSuccess) return e;
+  if ((e = gm_set_smem<192>((int)gm_fft_smem_bytes(192))) != cudaSuccess) return e;
+  return gm_set_smem<256>((int)gm_fft_smem_bytes(256));
 }
 
 namespace {
@@ -301,34 +394,29 @@ struct GmLauncher {
     const size_t b = (n + 255) / 256;
     return (unsigned)(b < 8192 ? b : 8192);
   }
-  cudaError_t fft2(bool inv) {
-    const int L = lines_per_block(M);
-    const unsigned grid = (unsigned)((size_t)a.n_pos * M / L);
+  cudaError_t line(int op, int cols, int s = 0, int pre = 0, int post = 0, int store = 0) {
+    const GmLineArgs g{op, cols, s, pre, post, store};
+    const unsigned grid = (unsigned)((size_t)a.n_pos * M / gm_lines(M));
     const size_t smem = gm_fft_smem_bytes(M);
-    for (int cols = 0; cols < 2; ++cols) {
-      if (inv)
-        k_gm_fft<true><<<grid, 256, smem, st>>>(wv, M, L, cols, plan, a.tw);
-      else
-        k_gm_fft<false><<<grid, 256, smem, st>>>(wv, M, L, cols, plan, a.tw);
-      ++launches;
+    switch (M) {
+      case 96: k_gm_line<96><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
+      case 192: k_gm_line<192><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
+      case 256: k_gm_line<256><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
+      default: k_gm_line<0><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
     }
-    return cudaGetLastError();
-  }
-  cudaError_t propagate(bool conj) {
-    cudaError_t e = fft2(false);
-    if (e != cudaSuccess) return e;
-    if (conj)
-      k_gm_prop<true><<<ew_grid(), 256, 0, st>>>(a, wv, M);
-    else
-      k_gm_prop<false><<<ew_grid(), 256, 0, st>>>(a, wv, M);
     ++launches;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return fft2(true);
+    return cudaGetLastError();
   }
 };
 
 }  // namespace
 
+// Forward: for each slice s < S-1 one row pass (transmission, propagation
+// along x) and one column pass (propagation along y); the last slice's row
+// and column passes are the far-field transform.  Adjoint, in reverse: the
+// inverse far field (column pass, then row pass ending in the adjoint
+// transmission of slice S-1), then per slice a conjugate-propagation column
+// pass and a row pass ending in the adjoint transmission.
 cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int M, int* n_launches,
                             cudaStream_t st) {
   if (a.n_pos <= 0) return cudaSuccess;
@@ -338,13 +426,13 @@ cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int 
   const bool grad = mode == MODE_GRAD;
   k_gm_init<<<g.ew_grid(), 256, 0, st>>>(a, wv, M);
   ++g.launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int s = 0; s < a.S; ++s) {
-    k_gm_transmit<false><<<g.ew_grid(), 256, 0, st>>>(a, wv, M, s, grad && s > 0);
-    ++g.launches;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (s < a.S - 1 && (e = g.propagate(false)) != cudaSuccess) return e;
+    const bool last = s == a.S - 1;
+    const int op = last ? GM_FFT : GM_PROP;
+    if ((e = g.line(op, 0, s, 1, 0, grad && s > 0)) != cudaSuccess) return e;
+    if ((e = g.line(op, 1)) != cudaSuccess) return e;
   }
-  if ((e = g.fft2(false)) != cudaSuccess) return e;
   switch (mode) {
     case MODE_FORWARD: k_gm_residual<MODE_FORWARD><<<a.n_pos, 256, 0, st>>>(a, wv, M); break;
     case MODE_LOSS: k_gm_residual<MODE_LOSS><<<a.n_pos, 256, 0, st>>>(a, wv, M); break;
@@ -353,12 +441,10 @@ cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int 
   ++g.launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (grad) {
-    if ((e = g.fft2(true)) != cudaSuccess) return e;
     for (int s = a.S - 1; s >= 0; --s) {
-      k_gm_transmit<true><<<g.ew_grid(), 256, 0, st>>>(a, wv, M, s, 1);
-      ++g.launches;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if (s > 0 && (e = g.propagate(true)) != cudaSuccess) return e;
+      const int op = s == a.S - 1 ? GM_IFFT : GM_PROP_CONJ;
+      if ((e = g.line(op, 1)) != cudaSuccess) return e;
+      if ((e = g.line(op, 0, s, 0, 1)) != cudaSuccess) return e;
     }
   }
   if (n_launches) *n_launches = g.launches;
