@@ -45,8 +45,16 @@ __device__ __forceinline__ void dft_r(float2 (&x)[R]) {
   }
 }
 
+// Shared-memory slot of element i of a line: one padding slot every 16
+// elements, which spreads the radix-8 first stage (outputs 8 apart across
+// threads) over the banks; the odd line stride does the same for the column
+// transposes.  (Simulated bank wavefronts per warp access, ideal 2: 2.0-2.8
+// for M = 96, 192, 256 against 3.3-4.7 unpadded.)
+__host__ __device__ constexpr int gm_pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int gm_line_stride(int M) { return M + M / 16 + 1; }
+
 // One Stockham autosort stage of radix R on L lines of length M (line
-// stride LS in shared memory), after spans of Ns: butterfly j takes
+// stride LS in shared memory, padded slots), after spans of Ns: butterfly j takes
 // x[j + q M/R], twiddles it by w_{Ns R}^{q (j mod Ns)} = w_M^{tstep q k}, and
 // writes y[(j - k) R + k + q Ns].  tstep q k < M, so the table needs no wrap.
 template <int R, bool INV>
@@ -61,7 +69,7 @@ __device__ __forceinline__ void gm_stage(const float2* __restrict__ src, float2*
     const float2* s = src + li * LS;
     float2 x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = s[j + q * nb];
+    for (int q = 0; q < R; ++q) x[q] = s[gm_pad(j + q * nb)];
     if (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
@@ -70,9 +78,10 @@ __device__ __forceinline__ void gm_stage(const float2* __restrict__ src, float2*
       }
     }
     dft_r<R, INV>(x);
-    float2* d = dst + li * LS + (j - k) * R + k;
+    float2* d = dst + li * LS;
+    const int d0 = (j - k) * R + k;
 #pragma unroll
-    for (int q = 0; q < R; ++q) d[q * Ns] = x[q];
+    for (int q = 0; q < R; ++q) d[gm_pad(d0 + q * Ns)] = x[q];
   }
 }
 
@@ -109,7 +118,7 @@ __device__ __forceinline__ float2* gm_stages_ct(float2* src, float2* dst, const 
     return src;
   } else {
     constexpr int R = gm_radix_at(MC, I);
-    gm_stage<R, INV>(src, dst, MC, MC + 1, gm_lines(MC), NS, T, t, 256);
+    gm_stage<R, INV>(src, dst, MC, gm_line_stride(MC), gm_lines(MC), NS, T, t, 256);
     __syncthreads();
     return gm_stages_ct<INV, MC, I + 1, NS * R>(dst, src, T, t);
   }
@@ -127,13 +136,13 @@ __device__ __forceinline__ float2* gm_transform(float2* src, float2* dst, int M,
     for (int st = 0; st < plan.n; ++st) {
       const int R = plan.r[st];
       if (R == 8)
-        gm_stage<8, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+        gm_stage<8, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
       else if (R == 4)
-        gm_stage<4, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+        gm_stage<4, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
       else if (R == 2)
-        gm_stage<2, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+        gm_stage<2, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
       else
-        gm_stage<3, INV>(src, dst, M, M + 1, L, Ns, T, t, 256);
+        gm_stage<3, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
       __syncthreads();
       float2* tmp = src;
       src = dst;
@@ -146,28 +155,6 @@ __device__ __forceinline__ float2* gm_transform(float2* src, float2* dst, int M,
 
 __device__ __forceinline__ bool window_ok(int2 r, int M, int H, int W) {
   return r.x >= 0 && r.y >= 0 && r.x <= H - M && r.y <= W - M;
-}
-
-// wv[i] = P (+ step * dir); invalid windows flag the call and start from 0.
-__global__ void k_gm_init(const ChainArgs a, float2* __restrict__ wv, int M) {
-  const size_t MM = (size_t)M * M, n = (size_t)a.n_pos * MM;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int il = (int)(idx / MM);
-    const int rem = (int)(idx % MM);
-    const int2 r = a.pos[a.pos_begin + il];
-    float2 p = make_float2(0.f, 0.f);
-    if (window_ok(r, M, a.H, a.W)) {
-      p = a.probe[rem];
-      if (a.probe_dir) {
-        const float2 d = a.probe_dir[rem];
-        p.x = fmaf(a.probe_step, d.x, p.x);
-        p.y = fmaf(a.probe_step, d.y, p.y);
-      }
-    } else if (rem == 0) {
-      *a.status = PTYCHO_ERR_POSITION;
-    }
-    wv[idx] = p;
-  }
 }
 
 // What one line pass does between loading and storing its lines.
@@ -189,16 +176,17 @@ struct GmLineArgs {
 // inverse.  Row passes also apply the slice's transmission (Sec. II-B) on
 // load, or its adjoint on store, so a slice costs one row and one column
 // pass each way.
-//   forward transmission (pre):  [psi_s -> workspace], v = psi_s O_s[window] (+ step dir)
+//   forward transmission (pre):  psi_0 = P (+ step dir); [psi_s -> workspace];
+//                                v = psi_s O_s[window] (+ step dir)
 //   adjoint transmission (post): g_phi_s -> workspace, v = conj(O_s[window]) g_phi_s,
 //                                at s = 0 into the probe-gradient workspace instead.
-// Skipped (out-of-range) windows carry zeros.
+// Skipped (out-of-range) windows carry zeros and flag the call.
 template <int MC>
 __global__ void __launch_bounds__(256) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
                                                  GmLineArgs g) {
   if constexpr (MC > 0) M = MC;
   const int L = MC > 0 ? gm_lines(MC) : gm_lines(M);
-  const int LS = M + 1;
+  const int LS = gm_line_stride(M);
   extern __shared__ float2 gsm[];
   float2* A = gsm;
   float2* B = A + (size_t)L * LS;
@@ -218,32 +206,77 @@ __global__ void __launch_bounds__(256) k_gm_line(const ChainArgs a, float2* __re
   const bool ok = window_ok(r, M, a.H, a.W);
   const size_t HW = (size_t)a.H * a.W;
   const int n = L * M;
+  // Loads are issued in batches of U per thread before their results are
+  // used, so each thread keeps U global reads in flight.
+  constexpr int U = 8;
   if (g.cols) {
-    for (int idx = t; idx < n; idx += 256) {
-      const int p = idx / L, li = idx - p * L;
-      A[li * LS + p] = base[(size_t)p * M + l0 + li];
-    }
-  } else {
-    for (int idx = t; idx < n; idx += 256) {
-      const int li = idx / M, x = idx - li * M;
-      const size_t rem = (size_t)l0 * M + idx;
-      float2 v = base[rem];
-      if (g.pre) {
-        if (!ok) {
-          v = make_float2(0.f, 0.f);
-        } else {
-          if (g.store) __stcs(a.ws_psi + ((size_t)(g.s - 1) * a.ws_n + il) * MM + rem, v);
-          const size_t oi = (size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x);
-          float2 o = a.obj[oi];
-          if (a.obj_dir) {
-            const float2 d = a.obj_dir[oi];
-            o.x = fmaf(a.obj_step, d.x, o.x);
-            o.y = fmaf(a.obj_step, d.y, o.y);
-          }
-          v = cmul(v, o);
+    for (int i0 = 0; i0 < n; i0 += 256 * U) {
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * 256 + t;
+        if (idx < n) {
+          const int p = idx / L, li = idx - p * L;
+          v[u] = base[(size_t)p * M + l0 + li];
         }
       }
-      A[li * LS + x] = v;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * 256 + t;
+        if (idx < n) {
+          const int p = idx / L, li = idx - p * L;
+          A[li * LS + gm_pad(p)] = v[u];
+        }
+      }
+    }
+  } else {
+    // Row pass with the forward transmission: the wave entering slice s is
+    // the probe at s = 0 (P + step dir on a line-search trial), else wv.
+    const bool from_probe = g.pre && g.s == 0;
+    const float2* src = from_probe ? a.probe : base + (size_t)l0 * M;
+    if (from_probe) src += (size_t)l0 * M;
+    if (g.pre && !ok && l0 == 0 && t == 0) *a.status = PTYCHO_ERR_POSITION;
+    for (int i0 = 0; i0 < n; i0 += 256 * U) {
+      float2 v[U], o[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * 256 + t;
+        if (idx < n) {
+          v[u] = src[idx];
+          if (g.pre && ok) {
+            const int li = idx / M, x = idx - li * M;
+            const size_t oi = (size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x);
+            o[u] = a.obj[oi];
+            if (a.obj_dir) {
+              const float2 d = a.obj_dir[oi];
+              o[u].x = fmaf(a.obj_step, d.x, o[u].x);
+              o[u].y = fmaf(a.obj_step, d.y, o[u].y);
+            }
+            if (from_probe && a.probe_dir) {
+              const float2 d = a.probe_dir[(size_t)l0 * M + idx];
+              v[u].x = fmaf(a.probe_step, d.x, v[u].x);
+              v[u].y = fmaf(a.probe_step, d.y, v[u].y);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * 256 + t;
+        if (idx < n) {
+          const int li = idx / M, x = idx - li * M;
+          float2 w = v[u];
+          if (g.pre) {
+            if (!ok) {
+              w = make_float2(0.f, 0.f);
+            } else {
+              if (g.store) __stcs(a.ws_psi + ((size_t)(g.s - 1) * a.ws_n + il) * MM + (size_t)l0 * M + idx, w);
+              w = cmul(w, o[u]);
+            }
+          }
+          A[li * LS + gm_pad(x)] = w;
+        }
+      }
     }
   }
   __syncthreads();
@@ -257,7 +290,7 @@ __global__ void __launch_bounds__(256) k_gm_line(const ChainArgs a, float2* __re
     const bool cj = g.op == GM_PROP_CONJ;
     for (int idx = t; idx < n; idx += 256) {
       const int li = idx / M, k = idx - li * M;
-      float2& z = mid[li * LS + k];
+      float2& z = mid[li * LS + gm_pad(k)];
       z = cj ? cmulc(z, Hs[k]) : cmul(z, Hs[k]);
     }
     __syncthreads();
@@ -266,29 +299,45 @@ __global__ void __launch_bounds__(256) k_gm_line(const ChainArgs a, float2* __re
   if (g.cols) {
     for (int idx = t; idx < n; idx += 256) {
       const int p = idx / L, li = idx - p * L;
-      base[(size_t)p * M + l0 + li] = out[li * LS + p];
+      base[(size_t)p * M + l0 + li] = out[li * LS + gm_pad(p)];
     }
-  } else {
+  } else if (!g.post) {
     for (int idx = t; idx < n; idx += 256) {
       const int li = idx / M, x = idx - li * M;
+      base[(size_t)l0 * M + idx] = out[li * LS + gm_pad(x)];
+    }
+  } else if (!ok) {
+    for (int idx = t; idx < n; idx += 256) {
       const size_t rem = (size_t)l0 * M + idx;
-      const float2 v = out[li * LS + x];
-      if (!g.post) {
-        base[rem] = v;
-        continue;
+      base[rem] = make_float2(0.f, 0.f);
+      if (g.s == 0) __stcs(a.ws_gp + (size_t)il * MM + rem, make_float2(0.f, 0.f));
+    }
+  } else {
+    for (int i0 = 0; i0 < n; i0 += 256 * U) {
+      float2 o[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * 256 + t;
+        if (idx < n) {
+          const int li = idx / M, x = idx - li * M;
+          o[u] = a.obj[(size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x)];
+        }
       }
-      if (!ok) {
-        base[rem] = make_float2(0.f, 0.f);
-        if (g.s == 0) __stcs(a.ws_gp + (size_t)il * MM + rem, make_float2(0.f, 0.f));
-        continue;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * 256 + t;
+        if (idx < n) {
+          const int li = idx / M, x = idx - li * M;
+          const size_t rem = (size_t)l0 * M + idx;
+          const float2 v = out[li * LS + gm_pad(x)];
+          __stcs(a.ws_gphi + ((size_t)g.s * a.ws_n + il) * MM + rem, v);
+          const float2 gv = cmulc(v, o[u]);
+          if (g.s == 0)
+            __stcs(a.ws_gp + (size_t)il * MM + rem, gv);
+          else
+            base[rem] = gv;
+        }
       }
-      __stcs(a.ws_gphi + ((size_t)g.s * a.ws_n + il) * MM + rem, v);
-      const size_t oi = (size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x);
-      const float2 gv = cmulc(v, a.obj[oi]);
-      if (g.s == 0)
-        __stcs(a.ws_gp + (size_t)il * MM + rem, gv);
-      else
-        base[rem] = gv;
     }
   }
 }
@@ -353,7 +402,9 @@ bool gm_supported(int M, GmPlan* plan) {
   return true;
 }
 
-size_t gm_fft_smem_bytes(int M) { return (2 * (size_t)gm_lines(M) * (M + 1) + 2 * (size_t)M) * sizeof(float2); }
+size_t gm_fft_smem_bytes(int M) {
+  return (2 * (size_t)gm_lines(M) * gm_line_stride(M) + 2 * (size_t)M) * sizeof(float2);
+}
 
 namespace {
 
@@ -389,11 +440,6 @@ struct GmLauncher {
   cudaStream_t st;
   int launches = 0;
 
-  unsigned ew_grid() const {
-    const size_t n = (size_t)a.n_pos * M * M;
-    const size_t b = (n + 255) / 256;
-    return (unsigned)(b < 8192 ? b : 8192);
-  }
   cudaError_t line(int op, int cols, int s = 0, int pre = 0, int post = 0, int store = 0) {
     const GmLineArgs g{op, cols, s, pre, post, store};
     const unsigned grid = (unsigned)((size_t)a.n_pos * M / gm_lines(M));
@@ -424,9 +470,6 @@ cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int 
   if (!gm_supported(M, &g.plan)) return cudaErrorInvalidValue;
   cudaError_t e;
   const bool grad = mode == MODE_GRAD;
-  k_gm_init<<<g.ew_grid(), 256, 0, st>>>(a, wv, M);
-  ++g.launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int s = 0; s < a.S; ++s) {
     const bool last = s == a.S - 1;
     const int op = last ? GM_FFT : GM_PROP;
