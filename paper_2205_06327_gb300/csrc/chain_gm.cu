@@ -3,9 +3,10 @@
 //
 // The chunk's positions advance through the multislice model (Sec. II-B)
 // together, slice by slice: their waves live in a global buffer wv[n][M][M].
-// Every pass loads a block of rows or columns of one wave into shared memory,
-// transforms them with mixed-radix (8/4/2/3) Stockham stages in natural
-// order, and writes them back.  Because the Fresnel factor is separable, a
+// Every pass transforms a block of rows or columns of one wave with
+// mixed-radix (8/4/2/3) Stockham stages in natural order: the first stage
+// reads the lines from the wave, later stages go through shared memory, the
+// last writes the lines back.  Because the Fresnel factor is separable, a
 // propagation is a row pass and a column pass, each running FFT, factor and
 // inverse on its lines; the transmission of a slice and its adjoint ride on
 // the row passes.  The amplitude residual of Eq. 1 is one pointwise kernel.
@@ -15,6 +16,18 @@
 #include "../../include/ptycho.h"
 #include "fft2d.cuh"
 #include "internal.h"
+
+// Line-pass block shape: threads, the most elements (lines x M) a block
+// takes, and the resident blocks per SM it is compiled for (register cap).
+#ifndef PTYCHO_GM_THREADS
+#define PTYCHO_GM_THREADS 256
+#endif
+#ifndef PTYCHO_GM_ELEMS
+#define PTYCHO_GM_ELEMS 4096
+#endif
+#ifndef PTYCHO_GM_MIN_BLOCKS
+#define PTYCHO_GM_MIN_BLOCKS 4
+#endif
 
 namespace ptycho {
 
@@ -53,38 +66,6 @@ __device__ __forceinline__ void dft_r(float2 (&x)[R]) {
 __host__ __device__ constexpr int gm_pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int gm_line_stride(int M) { return M + M / 16 + 1; }
 
-// One Stockham autosort stage of radix R on L lines of length M (line
-// stride LS in shared memory, padded slots), after spans of Ns: butterfly j takes
-// x[j + q M/R], twiddles it by w_{Ns R}^{q (j mod Ns)} = w_M^{tstep q k}, and
-// writes y[(j - k) R + k + q Ns].  tstep q k < M, so the table needs no wrap.
-template <int R, bool INV>
-__device__ __forceinline__ void gm_stage(const float2* __restrict__ src, float2* __restrict__ dst, int M, int LS,
-                                         int L, int Ns, const float2* __restrict__ T, int t, int nt) {
-  const int nb = M / R;
-  const int tstep = M / (Ns * R);
-  for (int idx = t; idx < L * nb; idx += nt) {
-    const int li = idx / nb;
-    const int j = idx - li * nb;
-    const int k = j % Ns;
-    const float2* s = src + li * LS;
-    float2 x[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = s[gm_pad(j + q * nb)];
-    if (Ns > 1) {
-#pragma unroll
-      for (int q = 1; q < R; ++q) {
-        const float2 w = T[tstep * q * k];
-        x[q] = INV ? cmulc(x[q], w) : cmul(x[q], w);
-      }
-    }
-    dft_r<R, INV>(x);
-    float2* d = dst + li * LS;
-    const int d0 = (j - k) * R + k;
-#pragma unroll
-    for (int q = 0; q < R; ++q) d[gm_pad(d0 + q * Ns)] = x[q];
-  }
-}
-
 // Radix schedule of a window: as many 8s as divide it, then 4, 2, then 3s.
 __host__ __device__ constexpr int gm_radix_at(int M, int i) {
   int m = M, k = 0;
@@ -102,55 +83,14 @@ __host__ __device__ constexpr int gm_n_stages(int M) {
   while (gm_radix_at(M, n) != 0) ++n;
   return n;
 }
-// Lines per block: the largest divisor of M with L M <= 4096.
+constexpr int kGmThreads = PTYCHO_GM_THREADS;
+
+// Lines per block: the largest divisor of M with L M <= PTYCHO_GM_ELEMS.
 __host__ __device__ constexpr int gm_lines(int M) {
   int best = 1;
-  for (int L = 1; L <= M && L * M <= 4096; ++L)
+  for (int L = 1; L <= M && L * M <= PTYCHO_GM_ELEMS; ++L)
     if (M % L == 0) best = L;
   return best;
-}
-
-// Stages with everything known at compile time (window MC): index
-// arithmetic folds to multiplies and shifts.
-template <bool INV, int MC, int I, int NS>
-__device__ __forceinline__ float2* gm_stages_ct(float2* src, float2* dst, const float2* T, int t) {
-  if constexpr (I == gm_n_stages(MC)) {
-    return src;
-  } else {
-    constexpr int R = gm_radix_at(MC, I);
-    gm_stage<R, INV>(src, dst, MC, gm_line_stride(MC), gm_lines(MC), NS, T, t, 256);
-    __syncthreads();
-    return gm_stages_ct<INV, MC, I + 1, NS * R>(dst, src, T, t);
-  }
-}
-
-// All stages of one transform of the block's lines; returns the buffer that
-// holds the result.  MC = 0: the radix schedule is read from the plan.
-template <bool INV, int MC>
-__device__ __forceinline__ float2* gm_transform(float2* src, float2* dst, int M, int L, const GmPlan& plan,
-                                                const float2* T, int t) {
-  if constexpr (MC > 0) {
-    return gm_stages_ct<INV, MC, 0, 1>(src, dst, T, t);
-  } else {
-    int Ns = 1;
-    for (int st = 0; st < plan.n; ++st) {
-      const int R = plan.r[st];
-      if (R == 8)
-        gm_stage<8, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
-      else if (R == 4)
-        gm_stage<4, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
-      else if (R == 2)
-        gm_stage<2, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
-      else
-        gm_stage<3, INV>(src, dst, M, gm_line_stride(M), L, Ns, T, t, 256);
-      __syncthreads();
-      float2* tmp = src;
-      src = dst;
-      dst = tmp;
-      Ns *= R;
-    }
-    return src;
-  }
 }
 
 __device__ __forceinline__ bool window_ok(int2 r, int M, int H, int W) {
@@ -169,20 +109,247 @@ struct GmLineArgs {
   int store;  // with pre: keep psi_s in the workspace
 };
 
+// Where a stage takes its inputs and puts its outputs: the block's shared
+// line buffers, the same times the propagation factor, or the wave in global
+// memory (first and last stage of a transform).
+enum : int { IO_SMEM = 0, IO_SMEM_H = 1, IO_GLOBAL = 2 };
+
+// The block's lines and what its first and last stages do with global
+// memory.  MC > 0: the window is a compile-time constant.
+template <int MC>
+struct GmCtx {
+  const ChainArgs& a;
+  GmLineArgs g;
+  int m, l;              // window and lines per block (when MC == 0)
+  int l0, il;            // first line, position in the chunk
+  int2 r;                // window corner (y, x)
+  bool ok, from_probe;
+  float2* base;          // this position's wave
+  const float2* in;      // row source of the first stage: the wave, or the probe at s = 0
+  const float2* Tst;     // per-stage twiddles (shared)
+  const float2* Hs;      // propagation factor hs[k] (shared)
+
+  __device__ __forceinline__ int M() const {
+    if constexpr (MC > 0) return MC; else return m;
+  }
+  __device__ __forceinline__ int L() const {
+    if constexpr (MC > 0) return gm_lines(MC); else return l;
+  }
+  // (y, x) and offset in the wave of element i of line li
+  __device__ __forceinline__ int y_of(int li, int i) const { return g.cols ? i : l0 + li; }
+  __device__ __forceinline__ int x_of(int li, int i) const { return g.cols ? l0 + li : i; }
+  __device__ __forceinline__ size_t at(int li, int i) const { return (size_t)y_of(li, i) * M() + x_of(li, i); }
+  __device__ __forceinline__ size_t obj_at(int li, int i) const {
+    return (size_t)g.s * a.H * a.W + (size_t)(r.x + y_of(li, i)) * a.W + (r.y + x_of(li, i));
+  }
+
+  // x[q] = element i0 + q di of line li, with the forward transmission when
+  // the pass carries it: all loads are issued before any is used.
+  template <int R>
+  __device__ __forceinline__ void load(float2 (&x)[R], int li, int i0, int di) const {
+    const size_t MM = (size_t)M() * M();
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = in[at(li, i0 + q * di)];
+    if (!g.pre) return;
+    if (!ok) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = make_float2(0.f, 0.f);
+      return;
+    }
+    float2 o[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const size_t oi = obj_at(li, i0 + q * di);
+      o[q] = a.obj[oi];
+      if (a.obj_dir) {
+        const float2 d = a.obj_dir[oi];
+        o[q].x = fmaf(a.obj_step, d.x, o[q].x);
+        o[q].y = fmaf(a.obj_step, d.y, o[q].y);
+      }
+      if (from_probe && a.probe_dir) {
+        const float2 d = a.probe_dir[at(li, i0 + q * di)];
+        x[q].x = fmaf(a.probe_step, d.x, x[q].x);
+        x[q].y = fmaf(a.probe_step, d.y, x[q].y);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (g.store) __stcs(a.ws_psi + ((size_t)(g.s - 1) * a.ws_n + il) * MM + at(li, i0 + q * di), x[q]);
+      x[q] = cmul(x[q], o[q]);
+    }
+  }
+
+  // element i0 + q di of line li = x[q], with the adjoint transmission when
+  // the pass carries it.
+  template <int R>
+  __device__ __forceinline__ void store(const float2 (&x)[R], int li, int i0, int di) const {
+    const size_t MM = (size_t)M() * M();
+    if (!g.post) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) base[at(li, i0 + q * di)] = x[q];
+      return;
+    }
+    if (!ok) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const size_t e = at(li, i0 + q * di);
+        base[e] = make_float2(0.f, 0.f);
+        if (g.s == 0) __stcs(a.ws_gp + (size_t)il * MM + e, make_float2(0.f, 0.f));
+      }
+      return;
+    }
+    float2 o[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) o[q] = a.obj[obj_at(li, i0 + q * di)];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const size_t e = at(li, i0 + q * di);
+      __stcs(a.ws_gphi + ((size_t)g.s * a.ws_n + il) * MM + e, x[q]);
+      const float2 gv = cmulc(x[q], o[q]);
+      if (g.s == 0)
+        __stcs(a.ws_gp + (size_t)il * MM + e, gv);
+      else
+        base[e] = gv;
+    }
+  }
+};
+
+// One Stockham autosort stage of radix R over the block's L lines of length
+// M, after spans of Ns: butterfly j takes x[j + q M/R], twiddles it by
+// w_{Ns R}^{q (j mod Ns)} (per-stage table at toff, contiguous in j mod Ns),
+// and writes y[(j - k) R + k + q Ns].  Rows map consecutive threads to
+// consecutive butterflies of a line, columns to the same butterfly of
+// consecutive lines, so the global first and last stages read and write
+// contiguous addresses; in the last stage (Ns = M/R) outputs land at j + q Ns
+// in natural order, so the propagation factor can be applied there.
+template <int R, bool INV, int IN, int OUT, int MC>
+__device__ __forceinline__ void gm_stage(const GmCtx<MC>& c, const float2* __restrict__ src,
+                                         float2* __restrict__ dst, int Ns, int toff, bool cj, int t) {
+  const int M = c.M(), L = c.L(), LS = gm_line_stride(M);
+  const int nb = M / R;
+  for (int idx = t; idx < L * nb; idx += kGmThreads) {
+    int li, j;
+    if (c.g.cols) {
+      j = idx / L;
+      li = idx - j * L;
+    } else {
+      li = idx / nb;
+      j = idx - li * nb;
+    }
+    const int k = j % Ns;
+    float2 x[R];
+    if constexpr (IN == IO_GLOBAL) {
+      c.template load<R>(x, li, j, nb);
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = src[li * LS + gm_pad(j + q * nb)];
+    }
+    if (Ns > 1) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        const float2 w = c.Tst[toff + (q - 1) * Ns + k];
+        x[q] = INV ? cmulc(x[q], w) : cmul(x[q], w);
+      }
+    }
+    dft_r<R, INV>(x);
+    const int d0 = (j - k) * R + k;
+    if constexpr (OUT == IO_GLOBAL) {
+      c.template store<R>(x, li, d0, Ns);
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int i = d0 + q * Ns;
+        float2 v = x[q];
+        if constexpr (OUT == IO_SMEM_H) v = cj ? cmulc(v, c.Hs[i]) : cmul(v, c.Hs[i]);
+        dst[li * LS + gm_pad(i)] = v;
+      }
+    }
+  }
+}
+
+// All stages of one transform of the block's lines, with the schedule known
+// at compile time.  Stage i reads the previous stage's buffer (stage 0: `rd`
+// or global memory) and writes b0 (i even) or b1 (i odd); returns the buffer
+// the last stage wrote when it writes shared memory.
+template <bool INV, int IN, int OUT, int MC, int I = 0, int NS = 1, int TOFF = 0>
+__device__ __forceinline__ float2* gm_tf_ct(const GmCtx<MC>& c, const float2* rd, float2* b0, float2* b1, bool cj,
+                                            int t) {
+  constexpr int NST = gm_n_stages(MC);
+  constexpr int R = gm_radix_at(MC, I);
+  constexpr bool LAST = I == NST - 1;
+  float2* wr = (I % 2 == 0) ? b0 : b1;
+  gm_stage<R, INV, I == 0 ? IN : IO_SMEM, LAST ? OUT : IO_SMEM, MC>(c, rd, wr, NS, TOFF, cj, t);
+  if constexpr (LAST) {
+    return wr;
+  } else {
+    __syncthreads();
+    return gm_tf_ct<INV, IN, OUT, MC, I + 1, NS * R, TOFF + (NS > 1 ? (R - 1) * NS : 0)>(c, wr, b0, b1, cj, t);
+  }
+}
+
+// The same with the schedule read from the plan.
+template <int R, bool INV, int IN, int OUT>
+__device__ __forceinline__ void gm_stage_rt(const GmCtx<0>& c, const float2* rd, float2* wr, int Ns, int toff,
+                                            bool cj, bool first, bool last, int t) {
+  if (first && last)
+    gm_stage<R, INV, IN, OUT, 0>(c, rd, wr, Ns, toff, cj, t);
+  else if (first)
+    gm_stage<R, INV, IN, IO_SMEM, 0>(c, rd, wr, Ns, toff, cj, t);
+  else if (last)
+    gm_stage<R, INV, IO_SMEM, OUT, 0>(c, rd, wr, Ns, toff, cj, t);
+  else
+    gm_stage<R, INV, IO_SMEM, IO_SMEM, 0>(c, rd, wr, Ns, toff, cj, t);
+}
+
+template <bool INV, int IN, int OUT>
+__device__ __forceinline__ float2* gm_tf_rt(const GmCtx<0>& c, const GmPlan& plan, const float2* rd, float2* b0,
+                                            float2* b1, bool cj, int t) {
+  int Ns = 1, toff = 0;
+  float2* wr = b0;
+  for (int i = 0; i < plan.n; ++i) {
+    const int R = plan.r[i];
+    const bool first = i == 0, last = i == plan.n - 1;
+    wr = (i % 2 == 0) ? b0 : b1;
+    if (R == 8)
+      gm_stage_rt<8, INV, IN, OUT>(c, rd, wr, Ns, toff, cj, first, last, t);
+    else if (R == 4)
+      gm_stage_rt<4, INV, IN, OUT>(c, rd, wr, Ns, toff, cj, first, last, t);
+    else if (R == 2)
+      gm_stage_rt<2, INV, IN, OUT>(c, rd, wr, Ns, toff, cj, first, last, t);
+    else
+      gm_stage_rt<3, INV, IN, OUT>(c, rd, wr, Ns, toff, cj, first, last, t);
+    if (!last) __syncthreads();
+    if (Ns > 1) toff += (R - 1) * Ns;
+    Ns *= R;
+    rd = wr;
+  }
+  return wr;
+}
+
+template <bool INV, int IN, int OUT, int MC>
+__device__ __forceinline__ float2* gm_tf(const GmCtx<MC>& c, const GmPlan& plan, const float2* rd, float2* b0,
+                                         float2* b1, bool cj, int t) {
+  if constexpr (MC > 0)
+    return gm_tf_ct<INV, IN, OUT, MC>(c, rd, b0, b1, cj, t);
+  else
+    return gm_tf_rt<INV, IN, OUT>(c, plan, rd, b0, b1, cj, t);
+}
+
 // One pass over L rows or columns of each wave.  The Fresnel factor is
 // separable, h(ky, kx) = h1(ky) h1(kx), so a propagation F^-1 h F is a 1-D
-// propagation of every row followed by one of every column: each pass keeps
-// its lines in shared memory through FFT, the factor hs[k] = h1(k)/M and the
-// inverse.  Row passes also apply the slice's transmission (Sec. II-B) on
-// load, or its adjoint on store, so a slice costs one row and one column
-// pass each way.
+// propagation of every row followed by one of every column: each pass runs
+// FFT, the factor hs[k] = h1(k)/M (applied by the FFT's last stage) and the
+// inverse on its lines, reading them from the wave in its first stage and
+// writing them back in its last.  Row passes also apply the slice's
+// transmission (Sec. II-B) on load, or its adjoint on store, so a slice
+// costs one row and one column pass each way.
 //   forward transmission (pre):  psi_0 = P (+ step dir); [psi_s -> workspace];
 //                                v = psi_s O_s[window] (+ step dir)
 //   adjoint transmission (post): g_phi_s -> workspace, v = conj(O_s[window]) g_phi_s,
 //                                at s = 0 into the probe-gradient workspace instead.
 // Skipped (out-of-range) windows carry zeros and flag the call.
 template <int MC>
-__global__ void __launch_bounds__(256) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
+__global__ void __launch_bounds__(kGmThreads, PTYCHO_GM_MIN_BLOCKS) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
                                                  GmLineArgs g) {
   if constexpr (MC > 0) M = MC;
   const int L = MC > 0 ? gm_lines(MC) : gm_lines(M);
@@ -190,172 +357,64 @@ __global__ void __launch_bounds__(256) k_gm_line(const ChainArgs a, float2* __re
   extern __shared__ float2 gsm[];
   float2* A = gsm;
   float2* B = A + (size_t)L * LS;
-  float2* T = B + (size_t)L * LS;
-  float2* Hs = T + M;
+  float2* Tst = B + (size_t)L * LS;  // sum over stages of (R - 1) Ns < M entries
+  float2* Hs = Tst + M;
   const int t = threadIdx.x;
-  for (int k = t; k < M; k += 256) {
-    T[k] = a.tw[k];
-    Hs[k] = a.hs[k];
+  {
+    const int nst = MC > 0 ? gm_n_stages(MC) : plan.n;
+    int Ns = 1, toff = 0;
+    for (int i = 0; i < nst; ++i) {
+      const int R = MC > 0 ? gm_radix_at(MC, i) : plan.r[i];
+      if (Ns > 1) {
+        const int tstep = M / (Ns * R);
+        for (int e = t; e < (R - 1) * Ns; e += kGmThreads) {
+          const int q = 1 + e / Ns, k = e - (q - 1) * Ns;
+          Tst[toff + e] = a.tw[tstep * q * k];
+        }
+        toff += (R - 1) * Ns;
+      }
+      Ns *= R;
+    }
+    for (int k = t; k < M; k += kGmThreads) Hs[k] = a.hs[k];
   }
-  const size_t MM = (size_t)M * M;
   const int g0 = blockIdx.x * L;  // first line of this block (L divides M)
   const int il = g0 / M;
   const int l0 = g0 - il * M;
-  float2* base = wv + (size_t)il * MM;
+  float2* base = wv + (size_t)il * M * M;
   const int2 r = a.pos[a.pos_begin + il];
   const bool ok = window_ok(r, M, a.H, a.W);
-  const size_t HW = (size_t)a.H * a.W;
-  const int n = L * M;
-  // Loads are issued in batches of U per thread before their results are
-  // used, so each thread keeps U global reads in flight.
-  constexpr int U = 8;
-  if (g.cols) {
-    for (int i0 = 0; i0 < n; i0 += 256 * U) {
-      float2 v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = i0 + u * 256 + t;
-        if (idx < n) {
-          const int p = idx / L, li = idx - p * L;
-          v[u] = base[(size_t)p * M + l0 + li];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = i0 + u * 256 + t;
-        if (idx < n) {
-          const int p = idx / L, li = idx - p * L;
-          A[li * LS + gm_pad(p)] = v[u];
-        }
-      }
-    }
-  } else {
-    // Row pass with the forward transmission: the wave entering slice s is
-    // the probe at s = 0 (P + step dir on a line-search trial), else wv.
-    const bool from_probe = g.pre && g.s == 0;
-    const float2* src = from_probe ? a.probe : base + (size_t)l0 * M;
-    if (from_probe) src += (size_t)l0 * M;
-    if (g.pre && !ok && l0 == 0 && t == 0) *a.status = PTYCHO_ERR_POSITION;
-    for (int i0 = 0; i0 < n; i0 += 256 * U) {
-      float2 v[U], o[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = i0 + u * 256 + t;
-        if (idx < n) {
-          v[u] = src[idx];
-          if (g.pre && ok) {
-            const int li = idx / M, x = idx - li * M;
-            const size_t oi = (size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x);
-            o[u] = a.obj[oi];
-            if (a.obj_dir) {
-              const float2 d = a.obj_dir[oi];
-              o[u].x = fmaf(a.obj_step, d.x, o[u].x);
-              o[u].y = fmaf(a.obj_step, d.y, o[u].y);
-            }
-            if (from_probe && a.probe_dir) {
-              const float2 d = a.probe_dir[(size_t)l0 * M + idx];
-              v[u].x = fmaf(a.probe_step, d.x, v[u].x);
-              v[u].y = fmaf(a.probe_step, d.y, v[u].y);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = i0 + u * 256 + t;
-        if (idx < n) {
-          const int li = idx / M, x = idx - li * M;
-          float2 w = v[u];
-          if (g.pre) {
-            if (!ok) {
-              w = make_float2(0.f, 0.f);
-            } else {
-              if (g.store) __stcs(a.ws_psi + ((size_t)(g.s - 1) * a.ws_n + il) * MM + (size_t)l0 * M + idx, w);
-              w = cmul(w, o[u]);
-            }
-          }
-          A[li * LS + gm_pad(x)] = w;
-        }
-      }
-    }
-  }
+  const bool from_probe = g.pre && g.s == 0;
+  const GmCtx<MC> c{a, g, M, L, l0, il, r, ok, from_probe, base, from_probe ? a.probe : base, Tst, Hs};
+  if (g.pre && !ok && l0 == 0 && t == 0) *a.status = PTYCHO_ERR_POSITION;
   __syncthreads();
-  float2* out;
   if (g.op == GM_FFT) {
-    out = gm_transform<false, MC>(A, B, M, L, plan, T, t);
+    gm_tf<false, IO_GLOBAL, IO_GLOBAL, MC>(c, plan, nullptr, A, B, false, t);
   } else if (g.op == GM_IFFT) {
-    out = gm_transform<true, MC>(A, B, M, L, plan, T, t);
+    gm_tf<true, IO_GLOBAL, IO_GLOBAL, MC>(c, plan, nullptr, A, B, false, t);
   } else {
-    float2* mid = gm_transform<false, MC>(A, B, M, L, plan, T, t);
     const bool cj = g.op == GM_PROP_CONJ;
-    for (int idx = t; idx < n; idx += 256) {
-      const int li = idx / M, k = idx - li * M;
-      float2& z = mid[li * LS + gm_pad(k)];
-      z = cj ? cmulc(z, Hs[k]) : cmul(z, Hs[k]);
-    }
+    float2* spec = gm_tf<false, IO_GLOBAL, IO_SMEM_H, MC>(c, plan, nullptr, A, B, cj, t);
     __syncthreads();
-    out = gm_transform<true, MC>(mid, mid == A ? B : A, M, L, plan, T, t);
-  }
-  if (g.cols) {
-    for (int idx = t; idx < n; idx += 256) {
-      const int p = idx / L, li = idx - p * L;
-      base[(size_t)p * M + l0 + li] = out[li * LS + gm_pad(p)];
-    }
-  } else if (!g.post) {
-    for (int idx = t; idx < n; idx += 256) {
-      const int li = idx / M, x = idx - li * M;
-      base[(size_t)l0 * M + idx] = out[li * LS + gm_pad(x)];
-    }
-  } else if (!ok) {
-    for (int idx = t; idx < n; idx += 256) {
-      const size_t rem = (size_t)l0 * M + idx;
-      base[rem] = make_float2(0.f, 0.f);
-      if (g.s == 0) __stcs(a.ws_gp + (size_t)il * MM + rem, make_float2(0.f, 0.f));
-    }
-  } else {
-    for (int i0 = 0; i0 < n; i0 += 256 * U) {
-      float2 o[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = i0 + u * 256 + t;
-        if (idx < n) {
-          const int li = idx / M, x = idx - li * M;
-          o[u] = a.obj[(size_t)g.s * HW + (size_t)(r.x + l0 + li) * a.W + (r.y + x)];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = i0 + u * 256 + t;
-        if (idx < n) {
-          const int li = idx / M, x = idx - li * M;
-          const size_t rem = (size_t)l0 * M + idx;
-          const float2 v = out[li * LS + gm_pad(x)];
-          __stcs(a.ws_gphi + ((size_t)g.s * a.ws_n + il) * MM + rem, v);
-          const float2 gv = cmulc(v, o[u]);
-          if (g.s == 0)
-            __stcs(a.ws_gp + (size_t)il * MM + rem, gv);
-          else
-            base[rem] = gv;
-        }
-      }
-    }
+    gm_tf<true, IO_SMEM, IO_GLOBAL, MC>(c, plan, spec, spec == A ? B : A, spec, cj, t);
   }
 }
 
 // Far field (unnormalised: M Psi) -> outputs (forward mode) or the residual
 // of Eq. 1: loss part per position (FP64, fixed order) and the adjoint seed
-// 2 d Psi/|Psi| / M, pre-scaled for the unnormalised inverse.  One block per position.
+// 2 d Psi/|Psi| / M, pre-scaled for the unnormalised inverse.  One block of
+// 1024 threads per position; each thread loads U elements before using them.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_gm_residual(const ChainArgs a, float2* __restrict__ wv, int M) {
-  __shared__ double red[8];
+__global__ void __launch_bounds__(1024) k_gm_residual(const ChainArgs a, float2* __restrict__ wv, int M) {
+  constexpr int NT = 1024, U = 4;
+  __shared__ double red[NT / 32];
   const int il = blockIdx.x, gi = a.pos_begin + il, t = threadIdx.x;
-  const size_t MM = (size_t)M * M;
+  const int MM = M * M;
   float2* w = wv + (size_t)il * MM;
   const bool ok = window_ok(a.pos[gi], M, a.H, a.W);
   const float inv_m = 1.0f / (float)M;
   if (MODE == MODE_FORWARD) {
     if (!ok) return;
-    for (int k = t; k < (int)MM; k += blockDim.x) {
+    for (int k = t; k < MM; k += NT) {
       const float2 z = make_float2(w[k].x * inv_m, w[k].y * inv_m);
       if (a.psi_out) a.psi_out[(size_t)gi * MM + k] = z;
       if (a.int_out) a.int_out[(size_t)gi * MM + k] = fmaf(z.x, z.x, z.y * z.y);
@@ -364,18 +423,32 @@ __global__ void __launch_bounds__(256) k_gm_residual(const ChainArgs a, float2* 
   }
   double lsum = 0.0;
   const float* Ii = a.meas + (size_t)gi * MM;
-  for (int k = t; k < (int)MM; k += blockDim.x) {
-    if (!ok) {
-      w[k] = make_float2(0.f, 0.f);
-      continue;
+  for (int k0 = 0; k0 < MM; k0 += NT * U) {
+    float2 z[U];
+    float I[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * NT + t;
+      if (k < MM && ok) {
+        z[u] = w[k];
+        I[u] = Ii[k];
+      }
     }
-    const float2 z = w[k];
-    const float A = sqrtf(Ii[k]);
-    const float mag = sqrtf(fmaf(z.x, z.x, z.y * z.y));
-    const float d = mag * inv_m - A;
-    lsum += (double)d * (double)d;
-    const float sc = mag > 0.0f ? (2.0f * d) / (mag * (float)M) : 0.0f;
-    w[k] = make_float2(z.x * sc, z.y * sc);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * NT + t;
+      if (k >= MM) continue;
+      if (!ok) {
+        w[k] = make_float2(0.f, 0.f);
+        continue;
+      }
+      const float A = sqrtf(I[u]);
+      const float mag = sqrtf(fmaf(z[u].x, z[u].x, z[u].y * z[u].y));
+      const float d = mag * inv_m - A;
+      lsum += (double)d * (double)d;
+      const float sc = mag > 0.0f ? (2.0f * d) / (mag * (float)M) : 0.0f;
+      w[k] = make_float2(z[u].x * sc, z[u].y * sc);
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
@@ -383,7 +456,7 @@ __global__ void __launch_bounds__(256) k_gm_residual(const ChainArgs a, float2* 
   __syncthreads();
   if (t == 0) {
     double tot = 0.0;
-    for (int k = 0; k < (int)(blockDim.x / 32); ++k) tot += red[k];
+    for (int k = 0; k < NT / 32; ++k) tot += red[k];
     a.loss_part[il] = ok ? tot : 0.0;
   }
 }
@@ -445,10 +518,10 @@ struct GmLauncher {
     const unsigned grid = (unsigned)((size_t)a.n_pos * M / gm_lines(M));
     const size_t smem = gm_fft_smem_bytes(M);
     switch (M) {
-      case 96: k_gm_line<96><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
-      case 192: k_gm_line<192><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
-      case 256: k_gm_line<256><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
-      default: k_gm_line<0><<<grid, 256, smem, st>>>(a, wv, M, plan, g); break;
+      case 96: k_gm_line<96><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
+      case 192: k_gm_line<192><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
+      case 256: k_gm_line<256><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
+      default: k_gm_line<0><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
     }
     ++launches;
     return cudaGetLastError();
@@ -477,9 +550,9 @@ cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int 
     if ((e = g.line(op, 1)) != cudaSuccess) return e;
   }
   switch (mode) {
-    case MODE_FORWARD: k_gm_residual<MODE_FORWARD><<<a.n_pos, 256, 0, st>>>(a, wv, M); break;
-    case MODE_LOSS: k_gm_residual<MODE_LOSS><<<a.n_pos, 256, 0, st>>>(a, wv, M); break;
-    default: k_gm_residual<MODE_GRAD><<<a.n_pos, 256, 0, st>>>(a, wv, M); break;
+    case MODE_FORWARD: k_gm_residual<MODE_FORWARD><<<a.n_pos, 1024, 0, st>>>(a, wv, M); break;
+    case MODE_LOSS: k_gm_residual<MODE_LOSS><<<a.n_pos, 1024, 0, st>>>(a, wv, M); break;
+    default: k_gm_residual<MODE_GRAD><<<a.n_pos, 1024, 0, st>>>(a, wv, M); break;
   }
   ++g.launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
