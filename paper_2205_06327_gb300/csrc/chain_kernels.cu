@@ -267,6 +267,16 @@ static cudaError_t prepare_m() {
 
 cudaError_t chain_prepare(int M) { return M == 128 ? prepare_m<128>() : prepare_m<64>(); }
 
+int chain_blocks_per_sm(int M) {
+  int n = 0;
+  const cudaError_t e =
+      M == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chain<128, MODE_GRAD>, Cfg<128>::T,
+                                                               chain_smem_bytes(128))
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chain<64, MODE_GRAD>, Cfg<64>::T,
+                                                               chain_smem_bytes(64));
+  return e == cudaSuccess ? n : 0;
+}
+
 template <int M>
 static cudaError_t launch_m(ChainMode mode, const ChainArgs& a, cudaStream_t st) {
   const dim3 grid(a.n_pos), block(Cfg<M>::T);

@@ -43,6 +43,7 @@ struct ChainArgs {
 
 // chain_kernels.cu
 int chain_threads(int M);
+int chain_blocks_per_sm(int M);  // resident gradient-mode blocks per SM (0 if unknown)
 size_t chain_smem_bytes(int M);
 cudaError_t chain_prepare(int M);  // raise the dynamic shared-memory limit
 cudaError_t launch_chain(int M, ChainMode mode, const ChainArgs& a, cudaStream_t st);

@@ -190,6 +190,11 @@ struct ptycho_plan_s {
   float2* g_probe = nullptr;
   uint32_t* d_cplanes = nullptr;  // BF16X3: [K, F][re_hi, re_lo, im_hi, im_lo][128][64] packed BF16 pairs
   // kernel timing: event pairs per kernel family, launch counters
+  // side stream for the object-gradient accumulation of a chunk's full chain
+  // waves while its partial last wave runs (fork/join by events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int wave = 0;               // chain blocks resident on the whole GPU at once
   struct Mark {
     int kind;
     cudaEvent_t start, stop;
@@ -221,6 +226,9 @@ void free_plan(ptycho_plan pl) {
   cudaFree(pl->g_obj);
   cudaFree(pl->g_probe);
   cudaFree(pl->d_cplanes);
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+  if (pl->side) cudaStreamDestroy(pl->side);
   if (pl->h_pos) cudaFreeHost(pl->h_pos);
   if (pl->h_scal) cudaFreeHost(pl->h_scal);
   delete pl;
@@ -322,11 +330,12 @@ int timed(ptycho_plan pl, int kind, int n_kernels, cudaStream_t st, F&& launch) 
   return PTYCHO_OK;
 }
 
-#define TIMED(kind, nk, expr)                                            \
-  do {                                                                   \
-    int rc_ = timed(pl, kind, nk, st, [&]() -> cudaError_t { return expr; }); \
-    if (rc_) return rc_;                                                 \
+#define TIMED_ON(stream, kind, nk, expr)                                      \
+  do {                                                                        \
+    int rc_ = timed(pl, kind, nk, stream, [&]() -> cudaError_t { return expr; }); \
+    if (rc_) return rc_;                                                      \
   } while (0)
+#define TIMED(kind, nk, expr) TIMED_ON(st, kind, nk, expr)
 
 ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, const ptycho_c64* obj,
                     const float* meas) {
@@ -368,40 +377,75 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
   a.obj_step = obj_step;
   a.probe_dir = probe_dir;
   a.probe_step = probe_step;
-  for (int c0 = 0, ci = 0; c0 < p.N; c0 += pl->chunk, ++ci) {
-    const int n = p.N - c0 < pl->chunk ? p.N - c0 : pl->chunk;
-    a.pos_begin = c0;
-    a.n_pos = n;
-    const ChainMode mode = !want_grad ? MODE_LOSS : (pl->ckpt_L ? MODE_GRAD_RC : MODE_GRAD);
+  const ChainMode mode = !want_grad ? MODE_LOSS : (pl->ckpt_L ? MODE_GRAD_RC : MODE_GRAD);
+  const size_t MM = (size_t)p.M * p.M;
+  auto launch_chain_for = [&](const ChainArgs& ca) -> int {
     int gm_launches = 0;
     if (pl->wv) {
-      TIMED(K_CHAIN, 0, launch_chain_gm(mode, a, pl->wv, p.M, &gm_launches, st));
+      TIMED(K_CHAIN, 0, launch_chain_gm(mode, ca, pl->wv, p.M, &gm_launches, st));
       pl->tm.launches += gm_launches;
       pl->tm.chain_launches += 1;
-    } else if (p.precision != PTYCHO_FP32)
-      TIMED(K_CHAIN, 1, launch_chain_tc(mode, a, pl->d_cplanes, p.precision == PTYCHO_FP16X3, st));
-    else
-      TIMED(K_CHAIN, 1, launch_chain(p.M, mode, a, st));
-    pl->tm.chain_positions += n;
-    if (grad_obj) {
-      AccumArgs g{};
-      g.pos = a.pos;
-      g.pos_begin = c0;
-      g.n_pos = n;
-      g.M = p.M;
-      g.S = p.S;
-      g.H = p.H;
-      g.W = p.W;
-      g.tile_h = p.tile_h ? p.tile_h : kDefaultTile;
-      g.tile_w = p.tile_w ? p.tile_w : kDefaultTile;
-      g.probe = a.probe;
-      g.ws_n = pl->chunk;
-      g.ws_psi = pl->ws_psi;
-      g.ws_gphi = pl->ws_gphi;
-      g.grad_obj = grad_obj;
-      g.accumulate = ci > 0;
-      g.patch_mode = pl->ckpt_L ? 1 : 0;
-      TIMED(K_ACCUM, 1, launch_accum_obj_grad(g, st));
+    } else if (p.precision != PTYCHO_FP32) {
+      TIMED(K_CHAIN, 1, launch_chain_tc(mode, ca, pl->d_cplanes, p.precision == PTYCHO_FP16X3, st));
+    } else {
+      TIMED(K_CHAIN, 1, launch_chain(p.M, mode, ca, st));
+    }
+    pl->tm.chain_positions += ca.n_pos;
+    return PTYCHO_OK;
+  };
+  // Object-gradient accumulation of positions [c0 + off, c0 + off + n) of
+  // the chunk, whose workspace slots start at off.
+  auto accum_for = [&](int c0, int off, int n, int accumulate, cudaStream_t on) -> int {
+    AccumArgs g{};
+    g.pos = a.pos;
+    g.pos_begin = c0 + off;
+    g.n_pos = n;
+    g.M = p.M;
+    g.S = p.S;
+    g.H = p.H;
+    g.W = p.W;
+    g.tile_h = p.tile_h ? p.tile_h : kDefaultTile;
+    g.tile_w = p.tile_w ? p.tile_w : kDefaultTile;
+    g.probe = a.probe;
+    g.ws_n = pl->chunk;
+    g.ws_psi = pl->ws_psi + (size_t)off * MM;
+    g.ws_gphi = pl->ws_gphi + (size_t)off * MM;
+    g.grad_obj = grad_obj;
+    g.accumulate = accumulate;
+    g.patch_mode = pl->ckpt_L ? 1 : 0;
+    TIMED_ON(on, K_ACCUM, 1, launch_accum_obj_grad(g, on));
+    return PTYCHO_OK;
+  };
+  for (int c0 = 0, ci = 0; c0 < p.N; c0 += pl->chunk, ++ci) {
+    const int n = p.N - c0 < pl->chunk ? p.N - c0 : pl->chunk;
+    // A chunk whose chain ends in a partial wave is launched as its full
+    // waves and the tail: the accumulation of the full waves then runs on the
+    // side stream, on the SMs the tail leaves idle.  The tail's workspace
+    // slots follow the full waves', and its accumulation is added second, so
+    // the summation order is fixed.
+    const int tail = (grad_obj && !pl->wv && pl->side && pl->wave > 0 && n > pl->wave) ? n % pl->wave : 0;
+    const int n1 = n - tail;
+    a.pos_begin = c0;
+    a.n_pos = n1;
+    int rc = launch_chain_for(a);
+    if (rc) return rc;
+    if (tail) {
+      CUDA_TRY(cudaEventRecord(pl->ev_fork, st));
+      ChainArgs at = a;
+      at.pos_begin = c0 + n1;
+      at.n_pos = tail;
+      at.ws_psi = pl->ws_psi + (size_t)n1 * MM;
+      at.ws_gphi = pl->ws_gphi + (size_t)n1 * MM;
+      at.ws_gp = pl->ws_gp + (size_t)n1 * MM;
+      at.loss_part = pl->loss_part + n1;
+      if ((rc = launch_chain_for(at)) != PTYCHO_OK) return rc;
+      CUDA_TRY(cudaStreamWaitEvent(pl->side, pl->ev_fork, 0));
+      if ((rc = accum_for(c0, 0, n1, ci > 0, pl->side)) != PTYCHO_OK) return rc;
+      CUDA_TRY(cudaEventRecord(pl->ev_join, pl->side));
+      CUDA_TRY(cudaStreamWaitEvent(st, pl->ev_join, 0));
+      if ((rc = accum_for(c0, n1, tail, 1, st)) != PTYCHO_OK) return rc;
+    } else if (grad_obj) {
+      if ((rc = accum_for(c0, 0, n, ci > 0, st)) != PTYCHO_OK) return rc;
     }
     if (grad_probe)
       TIMED(K_PROBE, 2, launch_probe_grad(pl->ws_gp, n, p.M, pl->gp_part, kProbeSplit, grad_probe, ci > 0, st));
@@ -496,6 +540,9 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
     if (chunk > blocks_per_wave) chunk -= chunk % blocks_per_wave;
   }
   pl->chunk = (int)chunk;
+  // Chain blocks resident on the GPU at once: the occupancy of the FP32
+  // gradient kernel, or one split-product block per SM (all of tensor memory).
+  if (!gm) pl->wave = pl->sm_count * (p.precision == PTYCHO_FP32 ? chain_blocks_per_sm(M) : 1);
 
   rc = PTYCHO_OK;
   if (!rc) rc = dev_alloc(&pl->d_tw, M, "twiddles");
@@ -514,6 +561,11 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
     planes = build_tc_planes(p, p.precision == PTYCHO_FP16X3);
     rc = dev_alloc(&pl->d_cplanes, planes.size(), "tensor-core operand planes");
   }
+  if (!rc && !gm &&
+      ((e = cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming)) != cudaSuccess))
+    rc = cuda_fail(e, "side stream");
   if (rc) {
     free_plan(pl);
     return rc;
