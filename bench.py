@@ -509,7 +509,12 @@ def run_multi(args, world, rank, local):
         dist.init_process_group("nccl", device_id=device)
     shapes = synth.multi_problem_shapes()
     probs, skipped = [], []
+    windows = {int(x) for x in args.windows.split(",")} if args.windows else None
     for p, (M, S, ny, nx, step) in enumerate(shapes):
+        if windows is not None and M not in windows:
+            continue
+        if args.problems and len(probs) >= args.problems:
+            break
         if not supported(M, args.precision):
             skipped.append(M)
             continue
@@ -556,7 +561,8 @@ def run_multi(args, world, rank, local):
         "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"{len(probs)} uneven problems of the 32 seeded shapes (windows 64-256, "
-                               "1-24 slices), one CUDA graph per gradient-descent iteration",
+                               "1-24 slices), one CUDA graph per gradient-descent iteration"
+                               + (f", windows {args.windows} only" if args.windows else ""),
                    "problems": len(probs), "skipped_windows": skipped,
                    "positions_per_iteration": per_it, "iterations": iters,
                    "tiles": {str(k): list(v) for k, v in tiles.items()},
@@ -589,6 +595,9 @@ def main(argv=None):
                     help="bf16x3 / fp16x3: 2-D transforms as hi/lo split DFT products on the tensor cores")
     ap.add_argument("--ckpt-every", type=int, default=None,
                     help="recompute mode: keep a wave checkpoint every L slices (0 = keep all)")
+    ap.add_argument("--windows", default="",
+                    help="workload 5: only the problems with these windows, e.g. 192,256 (profiling cases)")
+    ap.add_argument("--problems", type=int, default=0, help="workload 5: the first N problems only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
