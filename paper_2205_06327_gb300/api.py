@@ -118,6 +118,21 @@ class Plan:
             t = t.to(self.device, non_blocking=True)
         return t.contiguous()
 
+    def _to_host(self, *ts):
+        """Device results to fresh pinned host tensors: asynchronous copies on the
+        current stream (pinned blocks come from torch's host caching allocator),
+        then one synchronisation."""
+        out = []
+        for t in ts:
+            if t is None:
+                out.append(None)
+                continue
+            h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+            h.copy_(t, non_blocking=True)
+            out.append(h)
+        torch.cuda.current_stream(self.device).synchronize()
+        return out
+
     def _inputs(self, pos, probe, obj, meas=None):
         g = self.geom
         pos = self._dev(pos, torch.int32, (g.N, 2), "pos")
@@ -139,8 +154,8 @@ class Plan:
             check(self.lib.ptycho_forward(self._h, _ptr(pos), _ptr(probe), _ptr(obj), _ptr(psi), _ptr(inten),
                                           _stream_handle(self.device)))
         if host:
-            psi = psi.cpu() if psi is not None else None
-            inten = inten.cpu() if inten is not None else None
+            with torch.cuda.device(self.device):
+                psi, inten = self._to_host(psi, inten)
         return psi, inten
 
     def loss_grad(self, pos, probe, obj, meas, want_obj: bool = True, want_probe: bool = True,
@@ -158,7 +173,8 @@ class Plan:
             check(self.lib.ptycho_loss_grad(self._h, _ptr(pos), _ptr(probe), _ptr(obj), _ptr(meas), _ptr(loss),
                                             _ptr(gO), _ptr(gP), _stream_handle(self.device)))
         if host:
-            return loss.cpu(), (gO.cpu() if gO is not None else None), (gP.cpu() if gP is not None else None)
+            with torch.cuda.device(self.device):
+                loss, gO, gP = self._to_host(loss, gO, gP)
         return loss, gO, gP
 
     def step(self, pos, probe: torch.Tensor, obj: torch.Tensor, meas, alpha_obj: float, alpha_probe: float,
