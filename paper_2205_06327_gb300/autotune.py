@@ -41,20 +41,22 @@ def _save(d: dict) -> None:
     os.replace(tmp, path)
 
 
-def key_for(geom: Geometry, precision: str) -> str:
-    return f"M{geom.M}_S{geom.S}_H{geom.H}_W{geom.W}_N{geom.N}_{precision}"
+def key_for(geom: Geometry, precision: str, ckpt_every: int = 0) -> str:
+    return f"M{geom.M}_S{geom.S}_H{geom.H}_W{geom.W}_N{geom.N}_{precision}" + (f"_rc{ckpt_every}" if ckpt_every else "")
 
 
 def tune_tile(geom: Geometry, pos, probe, obj, meas, device, precision: str = "fp32",
-              candidates=CANDIDATES, reps: int = 2, use_cache: bool = True) -> tuple[int, int]:
-    """Fastest accumulation tile (rows, cols) for this shape, measured on these inputs."""
-    key = key_for(geom, precision)
+              candidates=CANDIDATES, reps: int = 2, use_cache: bool = True, ckpt_every: int = 0) -> tuple[int, int]:
+    """Fastest accumulation tile (rows, cols) for this shape, measured on these inputs
+    (recompute mode reads finished patches instead of two wave arrays: tuned separately)."""
+    key = key_for(geom, precision, ckpt_every)
     cache = _load() if use_cache else {}
     if key in cache:
         return tuple(cache[key]["tile"])
     results = {}
     for tile in candidates:
-        plan = Plan(geom, device, tile=tile, timing=True, async_check=True, precision=precision)
+        plan = Plan(geom, device, tile=tile, timing=True, async_check=True, precision=precision,
+                    ckpt_every=ckpt_every)
         plan.loss_grad(pos, probe, obj, meas)  # warm-up
         plan.timing(reset=True)
         for _ in range(reps):

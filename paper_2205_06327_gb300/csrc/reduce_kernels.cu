@@ -20,13 +20,21 @@ __device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p);
 
 constexpr int kAccThreads = 256;
 
-constexpr int kAccUnroll = 4;  // positions whose loads are in flight together
+// Accumulation shape: positions whose loads are in flight together, and
+// resident blocks per SM the kernel is compiled for.
+#ifndef PTYCHO_ACC_UNROLL
+#define PTYCHO_ACC_UNROLL 4
+#endif
+#ifndef PTYCHO_ACC_MIN_BLOCKS
+#define PTYCHO_ACC_MIN_BLOCKS 2
+#endif
+constexpr int kAccUnroll = PTYCHO_ACC_UNROLL;
 constexpr int kAccPPT = 4;     // pixels per thread per pixel group
 
 // One block owns one (tile, slice).  The tile's pixels are processed in
 // groups of kAccPPT * 256; for each group the block walks the positions whose
 // window meets the group's rows, in ascending order.
-__global__ void __launch_bounds__(kAccThreads, 2) k_accum_obj_grad(const AccumArgs a) {
+__global__ void __launch_bounds__(kAccThreads, PTYCHO_ACC_MIN_BLOCKS) k_accum_obj_grad(const AccumArgs a) {
   __shared__ int2 lpos[kAccThreads];
   __shared__ int lidx[kAccThreads];
   __shared__ int wcount[kAccThreads / 32];
