@@ -79,3 +79,45 @@ def start_object(wl, kind: str, seed: int = 0):
 def to_dev(a, dtype, device):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).to(device)
+
+
+# ------------------------------------------------------------------ process-pool oracle pieces
+# Workers of a spawn pool rebuild the seeded workload themselves (the inputs
+# are deterministic), so only positions, detector frames and small results
+# cross the process boundary.
+
+_POOL_STATE: dict = {}
+
+
+def pool_init(workload_fn: str, start_kind: str, start_seed: int) -> None:
+    wl = getattr(synth, workload_fn)()
+    _POOL_STATE["wl"] = wl
+    _POOL_STATE["probe"] = c64(wl.probe)
+    _POOL_STATE["truth"] = c64(wl.obj)
+    _POOL_STATE["start"] = c64(start_object(wl, start_kind, start_seed))
+    _POOL_STATE["h"] = propagator(wl)
+
+
+def pool_intensities(idx):
+    """Oracle intensities |G|^2 at the true object for positions idx (float64)."""
+    st = _POOL_STATE
+    return orc.intensities(st["probe"], st["truth"], st["wl"].pos[idx], st["h"])
+
+
+def pool_region_grad(args):
+    """One position's dF/dO (oracle, FP64) and the FP32 error model's, both
+    restricted to slices `ss` and the pixel block [y0, y1) x [x0, x1)."""
+    i, I_i, ss, y0, y1, x0, x1 = args
+    st = _POOL_STATE
+    wl, M = st["wl"], st["wl"].M
+    r = wl.pos[i]
+    _, gO_i, _ = orc.position_loss_grad(st["probe"], st["start"], r, I_i.astype(np.float64), st["h"])
+    _, f32, _ = fp32_chain_loss_grad(st["probe"], st["start"][:, r[0]:r[0] + M, r[1]:r[1] + M],
+                                     np.array([[0, 0]]), I_i[None], st["h"])
+    out = np.zeros((2, len(ss), y1 - y0, x1 - x0), np.complex128)
+    ya, yb = max(y0, r[0]), min(y1, r[0] + M)
+    xa, xb = max(x0, r[1]), min(x1, r[1] + M)
+    if ya < yb and xa < xb:
+        out[0, :, ya - y0:yb - y0, xa - x0:xb - x0] = gO_i[ss][:, ya - r[0]:yb - r[0], xa - r[1]:xb - r[1]]
+        out[1, :, ya - y0:yb - y0, xa - x0:xb - x0] = f32[ss][:, ya - r[0]:yb - r[0], xa - r[1]:xb - r[1]]
+    return out

@@ -428,6 +428,23 @@ def test_generic_windows(dev, M, S, ny, nx, step):
     _check(wl, start_object(wl, "perturbed", 4), I, dev)
 
 
+@pytest.mark.parametrize("M,S,ny,nx,step", [(8, 2, 2, 2, 3), (81, 2, 2, 2, 9)])
+def test_generic_window_extremes(dev, M, S, ny, nx, step):
+    """The smallest window (one radix-8 stage: the first stage reads and the last
+    writes the wave) and a pure radix-3 window."""
+    wl = synth.workload_random(M, S, ny, nx, step, seed=120 + M, amp_jitter=0.1)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 6), I, dev)
+
+
+def test_generic_window_maximum_size(dev):
+    """The largest window the path takes, M = 4096 (one line per block, the
+    runtime radix schedule 8 8 8 8, the largest shared-memory request)."""
+    wl = synth.workload_random(4096, 1, 1, 1, 8, seed=120 + 4096, amp_jitter=0.1)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 6), I, dev)
+
+
 def test_generic_window_forward_and_chunks(dev):
     """Forward far field, and a workspace cap that splits the positions into chunks."""
     wl = synth.workload_random(96, 2, 3, 4, 11, seed=97, amp_jitter=0.1)
