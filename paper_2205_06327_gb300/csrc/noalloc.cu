@@ -127,7 +127,7 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
   for (int k = 0; k < M; ++k) {
     const double ang = -two_pi * (double)k / (double)M;
     tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    const double f = (double)(k < M / 2 ? k : k - M) / ((double)M * p.pixel_A);
+    const double f = (double)(k <= (M - 1) / 2 ? k : k - M) / ((double)M * p.pixel_A);
     const double ph = -M_PI * p.lambda_A * p.dz_A * f * f;
     hs[k] = make_float2((float)(std::cos(ph) / M), (float)(std::sin(ph) / M));
   }

@@ -109,7 +109,7 @@ std::vector<uint32_t> build_tc_planes(const ptycho_params& p, bool f16) {
   std::vector<uint32_t> out((size_t)2 * 4 * M * (M / 2));
   std::vector<double> h1r(M), h1i(M);
   for (int k = 0; k < M; ++k) {
-    const double f = (double)(k < M / 2 ? k : k - M) / ((double)M * p.pixel_A);
+    const double f = (double)(k <= (M - 1) / 2 ? k : k - M) / ((double)M * p.pixel_A);
     const double ph = -M_PI * p.lambda_A * p.dz_A * f * f;
     h1r[k] = std::cos(ph);
     h1i[k] = std::sin(ph);
@@ -504,8 +504,8 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   for (int k = 0; k < M; ++k) {
     const double ang = -two_pi * (double)k / (double)M;
     tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    // fftfreq(M, pixel): k/(M*pixel) for k < M/2, (k-M)/(M*pixel) otherwise
-    const double f = (double)(k < M / 2 ? k : k - M) / ((double)M * p.pixel_A);
+    // fftfreq(M, pixel): k/(M*pixel) for k <= (M-1)/2, (k-M)/(M*pixel) otherwise (odd M too)
+    const double f = (double)(k <= (M - 1) / 2 ? k : k - M) / ((double)M * p.pixel_A);
     const double ph = -M_PI * p.lambda_A * p.dz_A * f * f;
     hs[k] = make_float2((float)(std::cos(ph) / M), (float)(std::sin(ph) / M));
   }
