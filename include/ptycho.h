@@ -84,7 +84,10 @@ typedef struct {
   float re, im;
 } ptycho_c64;
 
-/* Problem description (Sec. II-B, Eq. 1).  Windows M in {64, 128}. */
+/* Problem description (Sec. II-B, Eq. 1).  Windows: M = 64 and 128 run the
+ * register-resident kernels; with PTYCHO_FP32 any other M = 2^a 3^b in
+ * [8, 4096] runs the generic line-pass path; the split precisions take
+ * M = 128 only.  Other windows give PTYCHO_ERR_UNSUPPORTED. */
 typedef struct {
   int32_t M;          /* probe window / detector side, pixels */
   int32_t S;          /* number of object slices */
@@ -164,6 +167,36 @@ PTYCHO_API int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const p
 PTYCHO_API int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj,
                 const float* meas_I, double alpha_obj, double alpha_probe,
                 int32_t line_search, double* loss_out, double* t_out, void* stream);
+
+/* Several independent reconstructions in one call (the batched workload:
+ * problems of different windows, slice counts and sizes).  Each problem has
+ * its own plan and arrays, as for the single-problem calls; two entries may
+ * not share a plan, and problems must not share output arrays.  The
+ * problems' work is enqueued on `stream` in order, so one call can be
+ * captured in one CUDA graph when every plan uses PTYCHO_FLAG_ASYNC_CHECK.
+ * The call never synchronises: loss_out must be a device pointer or NULL.
+ * Results are bit-identical to the single-problem calls.  On an error the
+ * message names the problem; the work of the problems before it stays
+ * enqueued.  The paper has no counterpart: it reconstructs one dataset at a
+ * time. */
+typedef struct {
+  ptycho_plan plan;
+  const int32_t* pos_yx;   /* [N][2] device */
+  ptycho_c64* probe;       /* [M][M] device (updated in place by ptycho_multi_step) */
+  ptycho_c64* obj;         /* [S][H][W] device (updated in place by ptycho_multi_step) */
+  const float* meas_I;     /* [N][M][M] device */
+  double* loss_out;        /* device, or NULL: F (before the step) */
+  ptycho_c64* grad_obj;    /* ptycho_multi_loss_grad: [S][H][W] device or NULL */
+  ptycho_c64* grad_probe;  /* ptycho_multi_loss_grad: [M][M] device or NULL */
+} ptycho_problem;
+
+/* ptycho_loss_grad for every problem. */
+PTYCHO_API int ptycho_multi_loss_grad(const ptycho_problem* problems, int32_t n, void* stream);
+
+/* ptycho_step with a fixed step (t = 1, no line search) for every problem,
+ * with the same alpha_obj, alpha_probe. */
+PTYCHO_API int ptycho_multi_step(const ptycho_problem* problems, int32_t n, double alpha_obj,
+                                 double alpha_probe, void* stream);
 
 /* Per-kernel-family device time and launch counts accumulated since the
  * last reset.  Times are filled only for plans created with

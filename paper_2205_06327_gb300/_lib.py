@@ -39,6 +39,7 @@ EXPORTED = [
     "ptycho_plan_create", "ptycho_plan_destroy", "ptycho_plan_info", "ptycho_plan_status",
     "ptycho_forward", "ptycho_loss_grad", "ptycho_step", "ptycho_plan_timing", "ptycho_loss_grad_noalloc",
     "ptycho_potential_to_transmission", "ptycho_potential_grad", "ptycho_last_error", "ptycho_version",
+    "ptycho_multi_loss_grad", "ptycho_multi_step",
 ]
 
 
@@ -62,6 +63,20 @@ class PtychoTiming(C.Structure):
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class PtychoProblem(C.Structure):
+    """One entry of a multi-problem call (ptycho_problem)."""
+    _fields_ = [
+        ("plan", C.c_void_p),
+        ("pos_yx", C.c_void_p),
+        ("probe", C.c_void_p),
+        ("obj", C.c_void_p),
+        ("meas_I", C.c_void_p),
+        ("loss_out", C.c_void_p),
+        ("grad_obj", C.c_void_p),
+        ("grad_probe", C.c_void_p),
+    ]
 
 
 class PtychoError(RuntimeError):
@@ -95,6 +110,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ptycho_loss_grad_noalloc": ([C.POINTER(PtychoParams), vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_potential_to_transmission": ([vp, vp, C.c_int64, dbl, vp], C.c_int),
         "ptycho_potential_grad": ([vp, vp, vp, C.c_int64, dbl, vp], C.c_int),
+        "ptycho_multi_loss_grad": ([C.POINTER(PtychoProblem), i32, vp], C.c_int),
+        "ptycho_multi_step": ([C.POINTER(PtychoProblem), i32, dbl, dbl, vp], C.c_int),
         "ptycho_last_error": ([], C.c_char_p),
         "ptycho_version": ([], C.c_char_p),
     }

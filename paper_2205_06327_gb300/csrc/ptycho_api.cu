@@ -160,6 +160,10 @@ std::vector<uint32_t> build_tc_planes(const ptycho_params& p, bool f16) {
 }
 
 constexpr int64_t kDefaultWorkspace = 8ll << 30;
+// Generic-window path: the most bytes of chunk waves (streamed by every pass)
+#ifndef PTYCHO_GM_WAVE_BYTES
+#define PTYCHO_GM_WAVE_BYTES (64ll << 20)
+#endif
 constexpr int kProbeSplit = 32;
 constexpr int kNormParts = 512;
 
@@ -525,7 +529,7 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   // generic-window path: keep the chunk's waves (streamed by every FFT pass)
   // within about half of the L2
   if (gm && chunk > 1) {
-    const int64_t l2cap = ((int64_t)64 << 20) / (int64_t)(MM * sizeof(float2));
+    const int64_t l2cap = (int64_t)PTYCHO_GM_WAVE_BYTES / (int64_t)(MM * sizeof(float2));
     if (chunk > l2cap) chunk = l2cap > 1 ? l2cap : 1;
   }
   if (chunk < 1) {
@@ -679,12 +683,14 @@ int ptycho_forward(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* pr
   return PTYCHO_OK;
 }
 
-int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
-                     const float* meas_I, double* loss_out, ptycho_c64* grad_obj, ptycho_c64* grad_probe,
-                     void* stream) {
-  g_last_error.clear();
+}  // extern "C"
+
+namespace {
+
+int loss_grad_impl(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
+                   const float* meas_I, double* loss_out, ptycho_c64* grad_obj, ptycho_c64* grad_probe,
+                   cudaStream_t st) {
   if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc;
   if ((rc = check_array(probe, "probe", true)) || (rc = check_array(obj, "obj", true)) ||
       (rc = check_array(meas_I, "meas_I", plan->p.N > 0)) || (rc = check_array(grad_obj, "grad_obj", false)) ||
@@ -697,14 +703,12 @@ int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* 
   return deliver_loss(plan, 0, loss_out, st);
 }
 
-int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj, const float* meas_I,
-                double alpha_obj, double alpha_probe, int32_t line_search, double* loss_out, double* t_out,
-                void* stream) {
-  g_last_error.clear();
+int step_impl(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj, const float* meas_I,
+              double alpha_obj, double alpha_probe, int32_t line_search, double* loss_out, double* t_out,
+              cudaStream_t st) {
   if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
   if (!std::isfinite(alpha_obj) || !std::isfinite(alpha_probe))
     return fail(PTYCHO_ERR_ARG, "step sizes must be finite");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const ptycho_params& p = plan->p;
   int rc;
   if ((rc = check_array(probe, "probe", true)) || (rc = check_array(obj, "obj", true)) ||
@@ -749,6 +753,70 @@ int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptyc
   }
   if (t_out) *t_out = t;
   return PTYCHO_OK;
+}
+
+// Run fn(problem) for every problem, in order, on st.  (Running the problems
+// concurrently on their own streams was measured slower on the batched
+// workload: the generic-window problems size their chunks to the L2 and then
+// compete for it.)  Returns the first error, tagged with the problem's index.
+template <class F>
+int run_multi(const ptycho_problem* probs, int32_t n, F&& fn) {
+  if (n < 0 || (n > 0 && !probs)) return fail(PTYCHO_ERR_ARG, "problems must be non-NULL and n >= 0");
+  for (int32_t i = 0; i < n; ++i) {
+    if (!probs[i].plan) return fail(PTYCHO_ERR_ARG, "problem " + std::to_string(i) + ": plan is NULL");
+    if (probs[i].loss_out && !is_device_ptr(probs[i].loss_out))
+      return fail(PTYCHO_ERR_ARG, "problem " + std::to_string(i) + ": loss_out must be a device pointer or NULL");
+    for (int32_t j = 0; j < i; ++j)
+      if (probs[j].plan == probs[i].plan)
+        return fail(PTYCHO_ERR_ARG, "problems " + std::to_string(j) + " and " + std::to_string(i) +
+                                        " share a plan");
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    const int rc = fn(probs[i]);
+    if (rc) {
+      g_last_error = "problem " + std::to_string(i) + ": " + g_last_error;
+      return rc;
+    }
+  }
+  return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
+                     const float* meas_I, double* loss_out, ptycho_c64* grad_obj, ptycho_c64* grad_probe,
+                     void* stream) {
+  g_last_error.clear();
+  return loss_grad_impl(plan, pos_yx, probe, obj, meas_I, loss_out, grad_obj, grad_probe,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj, const float* meas_I,
+                double alpha_obj, double alpha_probe, int32_t line_search, double* loss_out, double* t_out,
+                void* stream) {
+  g_last_error.clear();
+  return step_impl(plan, pos_yx, probe, obj, meas_I, alpha_obj, alpha_probe, line_search, loss_out, t_out,
+                   static_cast<cudaStream_t>(stream));
+}
+
+int ptycho_multi_loss_grad(const ptycho_problem* problems, int32_t n, void* stream) {
+  g_last_error.clear();
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return run_multi(problems, n, [&](const ptycho_problem& q) {
+    return loss_grad_impl(q.plan, q.pos_yx, q.probe, q.obj, q.meas_I, q.loss_out, q.grad_obj, q.grad_probe, st);
+  });
+}
+
+int ptycho_multi_step(const ptycho_problem* problems, int32_t n, double alpha_obj, double alpha_probe,
+                      void* stream) {
+  g_last_error.clear();
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return run_multi(problems, n, [&](const ptycho_problem& q) {
+    return step_impl(q.plan, q.pos_yx, q.probe, q.obj, q.meas_I, alpha_obj, alpha_probe, 0, q.loss_out, nullptr,
+                     st);
+  });
 }
 
 int ptycho_potential_to_transmission(const float* V, ptycho_c64* obj, int64_t n, double sigma, void* stream) {

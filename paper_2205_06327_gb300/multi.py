@@ -3,8 +3,9 @@
 Each problem keeps its own plan (tables, workspace), device tensors and
 shape; one gradient-descent iteration of all problems -- for every problem the
 loss, both gradients (Eq. 1, Eq. 2) and the in-place update of O and P -- is
-captured once in a CUDA graph and replayed, so an iteration costs one graph
-launch however many problems and kernels it contains.  The workspace budget
+one library call (ptycho_multi_step), captured once in a CUDA graph and
+replayed, so an iteration costs one graph launch however many problems and
+kernels it contains.  The workspace budget
 is shared: each plan gets ``workspace_bytes / n_problems`` and chunks its
 positions to fit.
 
@@ -14,7 +15,6 @@ precisions take M = 128.  ``supported(M)`` says which.
 """
 from __future__ import annotations
 
-import ctypes as C
 from dataclasses import dataclass
 
 import torch
@@ -65,15 +65,33 @@ class MultiProblem:
     def positions_per_iteration(self) -> int:
         return sum(p.geom.N for p in self.problems)
 
-    def step_all(self, alpha_obj: float, alpha_probe: float) -> None:
-        """One fixed-step gradient-descent iteration of every problem, eagerly."""
-        stream = _stream_handle(self.device)
-        t = C.c_double(0.0)
+    def _entries(self, grads=None):
+        arr = (_lib.PtychoProblem * len(self.problems))()
         for i, (p, plan) in enumerate(zip(self.problems, self.plans)):
-            lp = self.loss.data_ptr() + 8 * i
-            _lib.check(plan.lib.ptycho_step(plan._h, p.pos.data_ptr(), p.probe.data_ptr(), p.obj.data_ptr(),
-                                            p.meas.data_ptr(), float(alpha_obj), float(alpha_probe), 0, lp,
-                                            C.byref(t), stream))
+            e = arr[i]
+            e.plan = plan._h.value
+            e.pos_yx, e.probe, e.obj, e.meas_I = (p.pos.data_ptr(), p.probe.data_ptr(), p.obj.data_ptr(),
+                                                  p.meas.data_ptr())
+            e.loss_out = self.loss.data_ptr() + 8 * i
+            if grads is not None:
+                e.grad_obj, e.grad_probe = grads[i][0].data_ptr(), grads[i][1].data_ptr()
+        return arr
+
+    def step_all(self, alpha_obj: float, alpha_probe: float) -> None:
+        """One fixed-step gradient-descent iteration of every problem: one library call."""
+        arr = self._entries()
+        with torch.cuda.device(self.device):
+            _lib.check(self.plans[0].lib.ptycho_multi_step(arr, len(self.problems), float(alpha_obj),
+                                                           float(alpha_probe), _stream_handle(self.device)))
+
+    def loss_grad_all(self):
+        """(F, dF/dO, dF/dP) of every problem (F in self.loss), one library call."""
+        grads = [(torch.empty_like(p.obj), torch.empty_like(p.probe)) for p in self.problems]
+        arr = self._entries(grads)
+        with torch.cuda.device(self.device):
+            _lib.check(self.plans[0].lib.ptycho_multi_loss_grad(arr, len(self.problems),
+                                                                _stream_handle(self.device)))
+        return self.loss, grads
 
     def capture(self, alpha_obj: float, alpha_probe: float, warmup: int = 1) -> None:
         """Capture one iteration of all problems in a CUDA graph (after eager warm-up

@@ -65,6 +65,43 @@ def test_graph_replay_matches_eager_and_oracle(dev):
     me.close()
 
 
+def test_multi_loss_grad_matches_single_calls(dev):
+    """One multi-problem call (a generic window among the problems) gives the
+    single-problem results bit for bit."""
+    from paper_2205_06327_gb300.multi import MultiProblem
+    specs = SPECS + [(96, 2, 2, 2, 13)]
+    probs, _ = _problems(dev, specs)
+    mp = MultiProblem(probs, dev)
+    loss, grads = mp.loss_grad_all()
+    torch.cuda.synchronize()
+    mp.check_status()
+    for i, (p, plan) in enumerate(zip(probs, mp.plans)):
+        l1, go, gp = plan.loss_grad(p.pos, p.probe, p.obj, p.meas)
+        torch.cuda.synchronize()
+        assert l1.item() == loss[i].item()
+        assert torch.equal(go, grads[i][0]) and torch.equal(gp, grads[i][1])
+    mp.close()
+
+
+def test_multi_call_argument_errors(dev):
+    from paper_2205_06327_gb300 import _lib
+    from paper_2205_06327_gb300.multi import MultiProblem
+    probs, _ = _problems(dev, SPECS[:2])
+    mp = MultiProblem(probs, dev)
+    lib = mp.plans[0].lib
+    arr = mp._entries()
+    arr[1].plan = arr[0].plan  # two entries sharing a plan
+    assert lib.ptycho_multi_step(arr, 2, 1e-3, 0.0, None) == _lib.PTYCHO_ERR_ARG
+    assert b"share a plan" in lib.ptycho_last_error()
+    arr = mp._entries()
+    host_loss = (_lib.C.c_double * 1)()
+    arr[1].loss_out = _lib.C.addressof(host_loss)  # host pointer: the call never synchronises
+    assert lib.ptycho_multi_loss_grad(arr, 2, None) == _lib.PTYCHO_ERR_ARG
+    assert b"problem 1" in lib.ptycho_last_error()
+    assert lib.ptycho_multi_step(arr, -1, 1e-3, 0.0, None) == _lib.PTYCHO_ERR_ARG
+    mp.close()
+
+
 def test_unsupported_window_is_refused(dev):
     from paper_2205_06327_gb300 import api
     from paper_2205_06327_gb300.multi import MultiProblem, Problem, supported
