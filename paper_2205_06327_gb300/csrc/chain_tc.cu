@@ -20,8 +20,8 @@
 // complex products use four real ones.  Pointwise work (transmission,
 // residual) stays FP32, the loss sum FP64.
 //
-// 256 threads: warp w owns tensor-memory lanes 32 (w % 4) .. + 31 (one row m
-// of the accumulator per thread) and half w / 4 of its columns.
+// 512 threads (or 256): warp w owns tensor-memory lanes 32 (w % 4) .. + 31
+// (one row m of the accumulator per thread) and column group w / 4.
 #include "../../include/ptycho.h"
 #include "internal.h"
 #include "tc_bf16.cuh"
@@ -35,6 +35,15 @@ constexpr int kPlaneBytes = TM * TM * 2;  // one BF16 plane
 constexpr uint32_t kColD = 0;             // D_re at columns [0,128), D_im at [128,256)
 constexpr uint32_t kColA = 256;           // A planes: re_hi, re_lo, im_hi, im_lo, 64 columns each
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at the maximum SM clock
+// Threads per block: 128 x (column groups).  Thread t owns tensor-memory lane
+// t % 128 and column group t / 128 (8 / groups chunks of 16 columns).
+#ifndef PTYCHO_TC_THREADS
+#define PTYCHO_TC_THREADS 512
+#endif
+constexpr int kTcThreads = PTYCHO_TC_THREADS;
+constexpr int kTcGroups = kTcThreads / 128;
+constexpr int kTcChunks = 8 / kTcGroups;  // 16-column chunks per thread
+static_assert(kTcThreads == 256 || kTcThreads == 512, "256 or 512 threads");
 
 __device__ __forceinline__ float2 cmul_tc(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -79,17 +88,17 @@ __device__ __forceinline__ void issue_sandwich_stage(uint32_t tm, uint32_t bpl_s
 }  // namespace
 
 template <int MODE, bool F16>
-__global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const uint32_t* __restrict__ cplanes) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_chain_tc(const ChainArgs a, const uint32_t* __restrict__ cplanes) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* bpl = smem;  // 4 planes of the B operand, K-major core-matrix layout
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 4 * kPlaneBytes);
   uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + 4 * kPlaneBytes + 8);
-  double* red = reinterpret_cast<double*>(smem + 4 * kPlaneBytes + 16);  // [8]
-  int* range_flag = reinterpret_cast<int*>(smem + 4 * kPlaneBytes + 80);
+  double* red = reinterpret_cast<double*>(smem + 4 * kPlaneBytes + 16);  // [kTcThreads / 32]
+  int* range_flag = reinterpret_cast<int*>(smem + 4 * kPlaneBytes + 16 + 8 * (kTcThreads / 32));
   const int t = threadIdx.x, w = t >> 5;
   const int m = t & 127;    // accumulator row (tensor-memory lane) of this thread
-  const int half = t >> 7;  // column half of this thread
-  const int c0 = 4 * half;  // its 16-column chunks: c0 .. c0 + 3
+  const int grp = t >> 7;           // column group of this thread
+  const int c0 = kTcChunks * grp;   // its 16-column chunks: c0 .. c0 + kTcChunks - 1
   const int il = blockIdx.x, gi = a.pos_begin + il;
   const int2 r = a.pos[gi];
   const int yi = r.x, xi = r.y;
@@ -126,7 +135,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
   // C planes (0 = propagator K, 1 = DFT F) into tensor-memory columns 256..511.
   auto load_planes = [&](int which) {
     const uint32_t* src = cplanes + (size_t)which * 4 * TM * 64;
-    for (int q = 2 * half; q < 2 * half + 2; ++q)
+    for (int q = (4 / kTcGroups) * grp; q < (4 / kTcGroups) * (grp + 1); ++q)
       for (int c = 0; c < 64; c += 16) {
         uint32_t rr[16];
 #pragma unroll
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
   // stage 1, transpose through the B operand, stage 2: D <- (C W C)^T
   auto sandwich = [&](bool conj) -> bool {
     if (!stage(conj)) return false;
-    for (int c = c0; c < c0 + 4; ++c) {
+    for (int c = c0; c < c0 + kTcChunks; ++c) {
       float re[16], im[16];
       read_d(c, re, im);
       write_b(c, re, im);
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
   bool ok = true;
   load_planes(0);
   // phi_0 = P * O_0, column-held: thread t owns x = t, rows y = 16 c + j
-  for (int c = c0; c < c0 + 4; ++c) {
+  for (int c = c0; c < c0 + kTcChunks; ++c) {
     float re[16], im[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
     const float2* ow = objw + (size_t)(s + 1) * HW;
     const float2* dw = dirw ? dirw + (size_t)(s + 1) * HW : nullptr;
     float2* wdst = MODE == MODE_GRAD ? a.ws_psi + ((size_t)s * a.ws_n + il) * MM : nullptr;
-    for (int c = c0; c < c0 + 4; ++c) {
+    for (int c = c0; c < c0 + kTcChunks; ++c) {
       float re[16], im[16];
       read_d(c, re, im);
 #pragma unroll
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
     if constexpr (MODE == MODE_FORWARD) {
       float2* po = a.psi_out ? a.psi_out + (size_t)gi * MM : nullptr;
       float* io = a.int_out ? a.int_out + (size_t)gi * MM : nullptr;
-      for (int c = c0; c < c0 + 4; ++c) {
+      for (int c = c0; c < c0 + kTcChunks; ++c) {
         float re[16], im[16];
         read_d(c, re, im);
 #pragma unroll
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
       // Amplitude residual of Eq. 1 and the seed of the adjoint.
       const float* Ii = a.meas + (size_t)gi * MM;
       double lsum = 0.0;
-      for (int c = c0; c < c0 + 4; ++c) {
+      for (int c = c0; c < c0 + kTcChunks; ++c) {
         float re[16], im[16];
         read_d(c, re, im);
 #pragma unroll
@@ -312,7 +321,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
       __syncthreads();
       if (t == 0) {
         double tot = 0.0;
-        for (int k = 0; k < 8; ++k) tot += red[k];
+        for (int k = 0; k < kTcThreads / 32; ++k) tot += red[k];
         a.loss_part[il] = tot;
       }
       if constexpr (MODE == MODE_GRAD) {
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
           float2* gdst = a.ws_gphi + ((size_t)s * a.ws_n + il) * MM;
           const float2* ow = objw + (size_t)s * HW;
           float2* gp = a.ws_gp + (size_t)il * MM;
-          for (int c = c0; c < c0 + 4; ++c) {
+          for (int c = c0; c < c0 + kTcChunks; ++c) {
             float re[16], im[16];
             read_d(c, re, im);
 #pragma unroll
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_tc(const ChainArgs a, const ui
   if (w == 0) tc::tmem_dealloc(tm, 512);
 }
 
-size_t chain_tc_smem_bytes() { return 4 * (size_t)kPlaneBytes + 128; }
+size_t chain_tc_smem_bytes() { return 4 * (size_t)kPlaneBytes + 256; }
 
 template <bool F16>
 static cudaError_t prepare_tc() {
@@ -384,9 +393,9 @@ template <bool F16>
 static cudaError_t launch_tc(ChainMode mode, const ChainArgs& a, const uint32_t* cplanes, cudaStream_t st) {
   const size_t smem = chain_tc_smem_bytes();
   switch (mode) {
-    case MODE_FORWARD: k_chain_tc<MODE_FORWARD, F16><<<a.n_pos, 256, smem, st>>>(a, cplanes); break;
-    case MODE_LOSS: k_chain_tc<MODE_LOSS, F16><<<a.n_pos, 256, smem, st>>>(a, cplanes); break;
-    case MODE_GRAD: k_chain_tc<MODE_GRAD, F16><<<a.n_pos, 256, smem, st>>>(a, cplanes); break;
+    case MODE_FORWARD: k_chain_tc<MODE_FORWARD, F16><<<a.n_pos, kTcThreads, smem, st>>>(a, cplanes); break;
+    case MODE_LOSS: k_chain_tc<MODE_LOSS, F16><<<a.n_pos, kTcThreads, smem, st>>>(a, cplanes); break;
+    case MODE_GRAD: k_chain_tc<MODE_GRAD, F16><<<a.n_pos, kTcThreads, smem, st>>>(a, cplanes); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
