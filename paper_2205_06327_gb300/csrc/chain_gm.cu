@@ -35,6 +35,101 @@ namespace {
 
 // Small DFT of a register array in natural order, forward kernel
 // exp(-2 pi i n k / R), inverse its conjugate, unnormalised.
+// w_R^e = exp(-2 pi i e / R) for the composite radices (the inverse uses the
+// conjugate), as exact constants.
+template <int R>
+struct Wr;
+template <>
+struct Wr<16> {
+  static constexpr float c[16] = {1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                                  0.f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                  -1.f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                                  0.f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+  static constexpr float s[16] = {0.f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                  -1.f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                                  0.f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                                  1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
+};
+template <>
+struct Wr<12> {
+  static constexpr float c[12] = {1.f, 0.86602540378443865f, 0.5f, 0.f, -0.5f, -0.86602540378443865f,
+                                  -1.f, -0.86602540378443865f, -0.5f, 0.f, 0.5f, 0.86602540378443865f};
+  static constexpr float s[12] = {0.f, -0.5f, -0.86602540378443865f, -1.f, -0.86602540378443865f, -0.5f,
+                                  0.f, 0.5f, 0.86602540378443865f, 1.f, 0.86602540378443865f, 0.5f};
+};
+template <>
+struct Wr<6> {
+  static constexpr float c[6] = {1.f, 0.5f, -0.5f, -1.f, -0.5f, 0.5f};
+  static constexpr float s[6] = {0.f, -0.86602540378443865f, -0.86602540378443865f, 0.f,
+                                 0.86602540378443865f, 0.86602540378443865f};
+};
+
+// v w_R^e (forward) or v conj(w_R^e) (inverse), with the trivial factors
+// (1, -i, -1, +i) as sign and swap operations.
+template <int R, int E, bool INV>
+__device__ __forceinline__ float2 mul_wr(float2 v) {
+  constexpr int e = E % R;
+  if constexpr (e == 0) {
+    return v;
+  } else if constexpr (4 * e == R) {
+    return mul_mi<INV>(v);
+  } else if constexpr (2 * e == R) {
+    return make_float2(-v.x, -v.y);
+  } else if constexpr (4 * e == 3 * R) {
+    return mul_mi<!INV>(v);
+  } else {
+    const float c = Wr<R>::c[e], sn = INV ? -Wr<R>::s[e] : Wr<R>::s[e];
+    return make_float2(fmaf(v.x, c, -v.y * sn), fmaf(v.x, sn, v.y * c));
+  }
+}
+
+// R = R1 R2 for the composite radices.
+template <int R>
+struct Split;
+template <>
+struct Split<16> {
+  static constexpr int R1 = 4, R2 = 4;
+};
+template <>
+struct Split<12> {
+  static constexpr int R1 = 4, R2 = 3;
+};
+template <>
+struct Split<6> {
+  static constexpr int R1 = 2, R2 = 3;
+};
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2 (&x)[R]);
+
+// Composite small DFT (one Cooley-Tukey step in registers): with n = R2 n1 + n2
+// and k = k1 + R1 k2, X[k] = sum_n2 w_R2^(n2 k2) w_R^(n2 k1) sum_n1 w_R1^(n1 k1) x[n].
+template <int R, bool INV>
+__device__ __forceinline__ void dft_composite(float2 (&x)[R]) {
+  constexpr int R1 = Split<R>::R1, R2 = Split<R>::R2;
+  float2 y[R];  // y[n2 R1 + k1]
+  static_for<0, R2>([&](auto n2c) {
+    constexpr int n2 = decltype(n2c)::value;
+    float2 u[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) u[n1] = x[R2 * n1 + n2];
+    dft_r<R1, INV>(u);
+    static_for<0, R1>([&](auto k1c) {
+      constexpr int k1 = decltype(k1c)::value;
+      y[n2 * R1 + k1] = mul_wr<R, n2 * k1, INV>(u[k1]);
+    });
+  });
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = y[n2 * R1 + k1];
+    dft_r<R2, INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = u[k2];
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(float2 (&x)[R]) {
   if constexpr (R == 2) {
@@ -52,9 +147,11 @@ __device__ __forceinline__ void dft_r(float2 (&x)[R]) {
     x[2] = csub(t2, mid);
   } else if constexpr (R == 4) {
     dft4<INV>(x[0], x[1], x[2], x[3]);
-  } else {
-    static_assert(R == 8, "radix 2, 3, 4 or 8");
+  } else if constexpr (R == 8) {
     dft8<INV>(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7]);
+  } else {
+    static_assert(R == 6 || R == 12 || R == 16, "radix 2, 3, 4, 6, 8, 12 or 16");
+    dft_composite<R, INV>(x);
   }
 }
 
@@ -66,11 +163,21 @@ __device__ __forceinline__ void dft_r(float2 (&x)[R]) {
 __host__ __device__ constexpr int gm_pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int gm_line_stride(int M) { return M + M / 16 + 1; }
 
-// Radix schedule of a window: as many 8s as divide it, then 4, 2, then 3s.
-__host__ __device__ constexpr int gm_radix_at(int M, int i) {
+// Radix schedule of a window: with big, greedily the largest radix of 16, 12,
+// 8, 6, 4, 3, 2 that divides what is left (fewer stages: fewer shared-memory
+// round trips, more registers per thread); else 8s, then 4, 2, 3.  Which
+// instances take the large radices is in GmTraits.
+#ifndef PTYCHO_GM_MAX_RADIX
+#define PTYCHO_GM_MAX_RADIX 16
+#endif
+__host__ __device__ constexpr int gm_radix_at(int M, int i, bool big = false) {
   int m = M, k = 0;
-  const int order[4] = {8, 4, 2, 3};
-  for (int o = 0; o < 4; ++o)
+  const int order16[7] = {16, 12, 8, 6, 4, 3, 2};
+  const int order8[4] = {8, 4, 2, 3};
+  const bool b = big && PTYCHO_GM_MAX_RADIX >= 16;
+  const int* order = b ? order16 : order8;
+  const int n_order = b ? 7 : 4;
+  for (int o = 0; o < n_order; ++o)
     while (m % order[o] == 0 && m > 1) {
       if (k == i) return order[o];
       m /= order[o];
@@ -78,12 +185,33 @@ __host__ __device__ constexpr int gm_radix_at(int M, int i) {
     }
   return 0;
 }
-__host__ __device__ constexpr int gm_n_stages(int M) {
+__host__ __device__ constexpr int gm_n_stages(int M, bool big = false) {
   int n = 0;
-  while (gm_radix_at(M, n) != 0) ++n;
+  while (gm_radix_at(M, n, big) != 0) ++n;
   return n;
 }
 constexpr int kGmThreads = PTYCHO_GM_THREADS;
+
+// Per-instance choices, measured on the batched workload's windows (chain
+// time of all its problems of that window): the large radices (16/12/6) and a
+// 128-register budget (2 blocks/SM) win for 256 (197 vs 215 ms); 96 takes the
+// large radices at 80 registers (39 vs 42 ms); 192 keeps radix 8 at 64
+// registers (368 ms against 385-405 ms with radix 12/16).
+template <int MC>
+struct GmTraits {
+  static constexpr bool big = false;
+  static constexpr int min_blocks = PTYCHO_GM_MIN_BLOCKS;
+};
+template <>
+struct GmTraits<256> {
+  static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16;
+  static constexpr int min_blocks = 2;
+};
+template <>
+struct GmTraits<96> {
+  static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16;
+  static constexpr int min_blocks = 3;
+};
 
 // Lines per block: the largest divisor of M with L M <= PTYCHO_GM_ELEMS.
 __host__ __device__ constexpr int gm_lines(int M) {
@@ -274,8 +402,8 @@ __device__ __forceinline__ void gm_stage(const GmCtx<MC>& c, const float2* __res
 template <bool INV, int IN, int OUT, int MC, int I = 0, int NS = 1, int TOFF = 0>
 __device__ __forceinline__ float2* gm_tf_ct(const GmCtx<MC>& c, const float2* rd, float2* b0, float2* b1, bool cj,
                                             int t) {
-  constexpr int NST = gm_n_stages(MC);
-  constexpr int R = gm_radix_at(MC, I);
+  constexpr int NST = gm_n_stages(MC, GmTraits<MC>::big);
+  constexpr int R = gm_radix_at(MC, I, GmTraits<MC>::big);
   constexpr bool LAST = I == NST - 1;
   float2* wr = (I % 2 == 0) ? b0 : b1;
   gm_stage<R, INV, I == 0 ? IN : IO_SMEM, LAST ? OUT : IO_SMEM, MC>(c, rd, wr, NS, TOFF, cj, t);
@@ -349,7 +477,7 @@ __device__ __forceinline__ float2* gm_tf(const GmCtx<MC>& c, const GmPlan& plan,
 //                                at s = 0 into the probe-gradient workspace instead.
 // Skipped (out-of-range) windows carry zeros and flag the call.
 template <int MC>
-__global__ void __launch_bounds__(kGmThreads, PTYCHO_GM_MIN_BLOCKS) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
+__global__ void __launch_bounds__(kGmThreads, GmTraits<MC>::min_blocks) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
                                                  GmLineArgs g) {
   if constexpr (MC > 0) M = MC;
   const int L = MC > 0 ? gm_lines(MC) : gm_lines(M);
@@ -361,10 +489,10 @@ __global__ void __launch_bounds__(kGmThreads, PTYCHO_GM_MIN_BLOCKS) k_gm_line(co
   float2* Hs = Tst + M;
   const int t = threadIdx.x;
   {
-    const int nst = MC > 0 ? gm_n_stages(MC) : plan.n;
+    const int nst = MC > 0 ? gm_n_stages(MC, GmTraits<MC>::big) : plan.n;
     int Ns = 1, toff = 0;
     for (int i = 0; i < nst; ++i) {
-      const int R = MC > 0 ? gm_radix_at(MC, i) : plan.r[i];
+      const int R = MC > 0 ? gm_radix_at(MC, i, GmTraits<MC>::big) : plan.r[i];
       if (Ns > 1) {
         const int tstep = M / (Ns * R);
         for (int e = t; e < (R - 1) * Ns; e += kGmThreads) {
