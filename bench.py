@@ -383,8 +383,7 @@ def run_gpu(args, world, rank, local, pool):
     torch.cuda.synchronize(device)
     plan.timing(reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks = ClockSampler(local, f"{args.clocks_csv}.r{rank}.csv" if args.clocks_csv else None)
     barrier(world, device)
     torch.cuda.synchronize(device)
     wall0 = time.perf_counter()
@@ -608,6 +607,8 @@ def main(argv=None):
     ap.add_argument("--windows", default="",
                     help="workload 5: only the problems with these windows, e.g. 192,256 (profiling cases)")
     ap.add_argument("--problems", type=int, default=0, help="workload 5: the first N problems only")
+    ap.add_argument("--clocks-csv", default="",
+                    help="also keep the raw nvidia-smi clock samples of the timed region (<path>.r<rank>.csv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
