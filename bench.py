@@ -14,7 +14,7 @@ per-step CUDA events.  ``e2e`` repeats the measurement through the public
 Python API with host (pinned) inputs and host results, copies included.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
 Under torchrun (N > 1) every rank runs an independent replica of the
-workload (the path has no data exchange between GPUs in this build); rank 0
+workload (the evaluation has no data exchange between GPUs); rank 0
 prints the line with the max time over ranks.
 """
 from __future__ import annotations

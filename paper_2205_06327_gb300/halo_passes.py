@@ -13,7 +13,7 @@ interval and a column interval, the vertical passes give column sums and the
 horizontal passes complete them: afterwards every buffer equals the global
 gradient restricted to its extended tile.
 
-On one GPU this build sums the gradient with the owner-computes tiled
+On one GPU the library sums the gradient with the owner-computes tiled
 accumulation instead; this module runs the decomposition over any
 torch.distributed process group (gloo ranks on CPU in the tests), with
 non-blocking point-to-point messages as in the paper's asynchronous passes.

@@ -1,7 +1,7 @@
 """Host logic of bench.py's multi-process path on CPU (gloo, world size 2).
 
 With N GPUs each rank runs an independent replica of the workload (the hot
-path has no data exchange between GPUs in this build); the ranks meet at a
+path has no data exchange between GPUs); the ranks meet at a
 barrier around the timed region and rank 0 reports the maximum time.
 """
 import os
