@@ -545,7 +545,12 @@ def run_multi(args, world, rank, local):
                                                   precision=args.precision, use_cache=False)
         pr.tile = tiles[pr.geom.M]
     mp = MultiProblem(probs, device, precision=args.precision)
+    for pl in mp.plans:
+        pl.timing(reset=True)
     mp.capture(1e-3, 1e-6, warmup=args.warmup)
+    # the library counts the kernels each call enqueues: warm-up iterations
+    # plus the captured one; a replay launches the captured iteration's kernels
+    launches_per_iter = sum(pl.timing(reset=True)["launches"] for pl in mp.plans) / (args.warmup + 1)
     iters = args.iterations
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(device)
@@ -576,7 +581,8 @@ def run_multi(args, world, rank, local):
                    "positions_per_iteration": per_it, "iterations": iters,
                    "tiles": {str(k): list(v) for k, v in tiles.items()},
                    "l2": "inputs larger than L2 in aggregate; no flush between graph replays"},
-        "gpu_launches": None,
+        "gpu_launches": int(round(launches_per_iter * iters)),
+        "gpu_launches_per_step": launches_per_iter,
         "clocks": {"sm_mhz": csum["sm_mhz"], "sm_max_mhz": csum["sm_max_mhz"], "reasons": csum["reasons"]},
         "final_loss_sum": float(mp.loss.sum().item()),
     }
