@@ -31,7 +31,13 @@
  *
  * Streams: work is enqueued on the stream given to each call (NULL = the
  * legacy default stream) and runs asynchronously unless stated otherwise;
- * outputs are valid once that stream has been synchronised.
+ * outputs are valid once that stream has been synchronised.  A plan's
+ * workspace serves one call at a time: calls on one plan must be ordered
+ * (the same stream, or streams the caller orders); different plans are
+ * independent.  Inside a gradient call the library may fork part of the
+ * work onto a stream of its own and join it back into the call's stream
+ * with events, so the call stays ordered on that stream and can be captured
+ * in a CUDA graph.
  *
  * Errors: every entry point returns PTYCHO_OK (0) or a negative code and
  * records a message retrievable with ptycho_last_error() (per host thread).
