@@ -31,10 +31,10 @@
 
 namespace ptycho {
 
-namespace {
+// Constants of the composite radices (outside the anonymous namespace: not
+// every radix is instantiated in every build).
+namespace gmr {
 
-// Small DFT of a register array in natural order, forward kernel
-// exp(-2 pi i n k / R), inverse its conjugate, unnormalised.
 // w_R^e = exp(-2 pi i e / R) for the composite radices (the inverse uses the
 // conjugate), as exact constants.
 template <int R>
@@ -64,25 +64,6 @@ struct Wr<6> {
                                  0.86602540378443865f, 0.86602540378443865f};
 };
 
-// v w_R^e (forward) or v conj(w_R^e) (inverse), with the trivial factors
-// (1, -i, -1, +i) as sign and swap operations.
-template <int R, int E, bool INV>
-__device__ __forceinline__ float2 mul_wr(float2 v) {
-  constexpr int e = E % R;
-  if constexpr (e == 0) {
-    return v;
-  } else if constexpr (4 * e == R) {
-    return mul_mi<INV>(v);
-  } else if constexpr (2 * e == R) {
-    return make_float2(-v.x, -v.y);
-  } else if constexpr (4 * e == 3 * R) {
-    return mul_mi<!INV>(v);
-  } else {
-    const float c = Wr<R>::c[e], sn = INV ? -Wr<R>::s[e] : Wr<R>::s[e];
-    return make_float2(fmaf(v.x, c, -v.y * sn), fmaf(v.x, sn, v.y * c));
-  }
-}
-
 // R = R1 R2 for the composite radices.
 template <int R>
 struct Split;
@@ -99,6 +80,31 @@ struct Split<6> {
   static constexpr int R1 = 2, R2 = 3;
 };
 
+}  // namespace gmr
+
+namespace {
+
+// Small DFT of a register array in natural order, forward kernel
+// exp(-2 pi i n k / R), inverse its conjugate, unnormalised.
+// v w_R^e (forward) or v conj(w_R^e) (inverse), with the trivial factors
+// (1, -i, -1, +i) as sign and swap operations.
+template <int R, int E, bool INV>
+__device__ __forceinline__ float2 mul_wr(float2 v) {
+  constexpr int e = E % R;
+  if constexpr (e == 0) {
+    return v;
+  } else if constexpr (4 * e == R) {
+    return mul_mi<INV>(v);
+  } else if constexpr (2 * e == R) {
+    return make_float2(-v.x, -v.y);
+  } else if constexpr (4 * e == 3 * R) {
+    return mul_mi<!INV>(v);
+  } else {
+    const float c = gmr::Wr<R>::c[e], sn = INV ? -gmr::Wr<R>::s[e] : gmr::Wr<R>::s[e];
+    return make_float2(fmaf(v.x, c, -v.y * sn), fmaf(v.x, sn, v.y * c));
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(float2 (&x)[R]);
 
@@ -106,7 +112,7 @@ __device__ __forceinline__ void dft_r(float2 (&x)[R]);
 // and k = k1 + R1 k2, X[k] = sum_n2 w_R2^(n2 k2) w_R^(n2 k1) sum_n1 w_R1^(n1 k1) x[n].
 template <int R, bool INV>
 __device__ __forceinline__ void dft_composite(float2 (&x)[R]) {
-  constexpr int R1 = Split<R>::R1, R2 = Split<R>::R2;
+  constexpr int R1 = gmr::Split<R>::R1, R2 = gmr::Split<R>::R2;
   float2 y[R];  // y[n2 R1 + k1]
   static_for<0, R2>([&](auto n2c) {
     constexpr int n2 = decltype(n2c)::value;
