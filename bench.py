@@ -150,6 +150,20 @@ class OraclePool:
         self.pool.join()
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_sample_indices(wl, n_sample: int) -> np.ndarray:
     if n_sample >= wl.N:
         return np.arange(wl.N)
@@ -311,7 +325,7 @@ def run_reference(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "positions_per_step": int(len(idx)), "M": wl.M, "S": wl.S,
                    "object": [wl.H, wl.W]},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                          "sample": f"{len(idx)} of {wl.N} positions per step (loss + object/probe gradient)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -462,7 +476,7 @@ def run_gpu(args, world, rank, local, pool):
         I_host = I.cpu().numpy()
         pool.evaluate(wl, idx[: min(len(idx), pool.cores)], I_host)  # warm the workers
         t_cpu = pool.evaluate(wl, idx, I_host)
-        cpu = {"value": len(idx) / t_cpu, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+        cpu = {"value": len(idx) / t_cpu, "unit": UNIT, "cores": pool.cores, "cpu": cpu_model(), "kind": "oracle",
                "sample": f"{len(idx)} of {wl.N} positions, one loss + object/probe gradient evaluation "
                          f"(FP64 NumPy, process pool)"}
 
