@@ -7,7 +7,6 @@ barrier around the timed region and rank 0 reports the maximum time.
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 

@@ -13,7 +13,6 @@ failure has already run every other test.
 """
 import ctypes as C
 
-import numpy as np
 import pytest
 
 from paper_2205_06327_gb300 import synth
