@@ -350,8 +350,8 @@ def run_gpu(args, world, rank, local, pool):
     obj0 = start_object(wl)
     geom = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
     tile = (0, 0)
-    if args.ckpt_every is None:  # the PbTiO3-shaped workload recomputes waves in the adjoint
-        args.ckpt_every = 5 if args.config == 3 else 0
+    if args.ckpt_every is None:  # the PbTiO3-shaped workload recomputes waves in the adjoint:
+        args.ckpt_every = 5 if args.config == 3 else 0  # ceil(sqrt(30)) = 6 checkpoints, interval 5
     plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=args.ckpt_every,
                     precision=args.precision)
     pos = torch.from_numpy(wl.pos).to(device)

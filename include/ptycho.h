@@ -115,8 +115,15 @@ typedef struct {
                          per position drops from (2S-1) to S + ceil(S/L) + L + 1
                          wave-sized buffers and the gradient accumulation reads
                          half the bytes, for about (S - ceil(S/L)) / (2S - 1)
-                         more FFT work.  L = 0 is used when L >= S. */
+                         more FFT work.  L = 0 is used when L >= S.
+                         PTYCHO_CKPT_AUTO: K = ceil(sqrt(S)) checkpoints,
+                         L = ceil(S / K), which keeps about 2 sqrt(S) waves
+                         per position.  Recompute mode
+                         applies to the FP32 path with M = 64 or 128; the
+                         other paths keep every wave. */
 } ptycho_params;
+
+#define PTYCHO_CKPT_AUTO (-1)  /* ptycho_params.ckpt_every: ceil(sqrt(S)) checkpoints */
 
 typedef struct ptycho_plan_s* ptycho_plan;
 

@@ -47,7 +47,7 @@ class Plan:
 
     def __init__(self, geom: Geometry, device: torch.device | int | str = "cuda",
                  workspace_bytes: int = 0, tile: tuple[int, int] = (0, 0), async_check: bool = False,
-                 timing: bool = False, ckpt_every: int = 0, precision: str = "fp32"):
+                 timing: bool = False, ckpt_every: int | str = 0, precision: str = "fp32"):
         if not torch.cuda.is_available():
             raise RuntimeError("libptycho needs a CUDA device; there is no CPU fallback")
         self.lib = _lib.load()
@@ -65,7 +65,7 @@ class Plan:
         p.flags = (_lib.PTYCHO_FLAG_ASYNC_CHECK if async_check else 0) | (_lib.PTYCHO_FLAG_TIMING if timing else 0)
         p.workspace_bytes = int(workspace_bytes)
         p.tile_h, p.tile_w = int(tile[0]), int(tile[1])
-        p.ckpt_every = int(ckpt_every)
+        p.ckpt_every = _lib.PTYCHO_CKPT_AUTO if ckpt_every == "auto" else int(ckpt_every)
         self._params = p
         h = C.c_void_p()
         with torch.cuda.device(self.device):

@@ -274,7 +274,8 @@ int validate_params(const ptycho_params& p) {
   const int th = p.tile_h ? p.tile_h : kDefaultTile, tw = p.tile_w ? p.tile_w : kDefaultTile;
   if (th < 1 || tw < 1 || th * tw > 8192) return fail(PTYCHO_ERR_ARG, "tile_h * tile_w must be in [1, 8192]");
   if ((int64_t)p.S * p.H * p.W > (int64_t)1 << 34) return fail(PTYCHO_ERR_ARG, "object too large");
-  if (p.ckpt_every < 0) return fail(PTYCHO_ERR_ARG, "ckpt_every must be >= 0");
+  if (p.ckpt_every < 0 && p.ckpt_every != PTYCHO_CKPT_AUTO)
+    return fail(PTYCHO_ERR_ARG, "ckpt_every must be >= 0 or PTYCHO_CKPT_AUTO");
   return PTYCHO_OK;
 }
 
@@ -516,9 +517,13 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
 
   // Workspace per position in flight (gradient mode).
   const size_t MM = (size_t)M * M;
-  pl->ckpt_L = (p.ckpt_every > 0 && p.ckpt_every < p.S && p.precision == PTYCHO_FP32 && fused_window(M))
-                   ? p.ckpt_every
-                   : 0;
+  int ckpt_req = p.ckpt_every;
+  if (ckpt_req == PTYCHO_CKPT_AUTO) {  // K = ceil(sqrt(S)) checkpoints, interval ceil(S / K)
+    int K = 1;
+    while (K * K < p.S) ++K;
+    ckpt_req = (p.S + K - 1) / K;
+  }
+  pl->ckpt_L = (ckpt_req > 0 && ckpt_req < p.S && p.precision == PTYCHO_FP32 && fused_window(M)) ? ckpt_req : 0;
   const bool gm = !fused_window(M);
   const int K = pl->ckpt_L ? (p.S + pl->ckpt_L - 1) / pl->ckpt_L : 0;
   const size_t psi_slots = pl->ckpt_L ? (size_t)(K - 1 + pl->ckpt_L + 1) : (size_t)(p.S - 1);

@@ -339,6 +339,24 @@ def test_recompute_mode_matches_store_all(dev, M, S, L):
     per = wl.M * wl.M * 8
     assert p_all.workspace_bytes // wl.N == (2 * S - 1) * per + per + 8
     assert p_rc.workspace_bytes // wl.N == (S + K - 1 + L + 1) * per + per + 8
+    p_all.close()
+    p_rc.close()
+
+
+def test_recompute_interval_auto(dev):
+    """ckpt_every = 'auto' keeps K = ceil(sqrt(S)) checkpoints, interval
+    ceil(S / K) (S = 10: K = 4, L = 3): the same plan, and the same bits, as
+    that interval given explicitly."""
+    wl = synth.workload_random(64, 10, 2, 3, 9, seed=77, amp_jitter=0.1)
+    I = (measurements(wl) * 1.3).astype(np.float32)
+    obj = start_object(wl, "perturbed", 7)
+    auto, expl = _plan(wl, dev, ckpt_every="auto"), _plan(wl, dev, ckpt_every=3)
+    assert auto.workspace_bytes == expl.workspace_bytes < _plan(wl, dev).workspace_bytes
+    auto.close()
+    expl.close()
+    a = _run(wl, obj, I, dev, ckpt_every="auto")
+    b = _run(wl, obj, I, dev, ckpt_every=3)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
 def test_recompute_mode_multislice_subset(dev):
