@@ -202,21 +202,37 @@ constexpr int kGmThreads = PTYCHO_GM_THREADS;
 // time of all its problems of that window): the large radices (16/12/6) and a
 // 128-register budget (2 blocks/SM) win for 256 (197 vs 215 ms); 96 takes the
 // large radices at 80 registers (39 vs 42 ms); 192 keeps radix 8 at 64
-// registers (368 ms against 385-405 ms with radix 12/16).
+// registers and 256 threads (368 ms against 385-405 ms with radix 12/16,
+// and 378-402 ms with 192, 384 or 512 threads per block).
+#ifndef PTYCHO_GM192_THREADS
+#define PTYCHO_GM192_THREADS 256
+#endif
+#ifndef PTYCHO_GM192_MIN_BLOCKS
+#define PTYCHO_GM192_MIN_BLOCKS PTYCHO_GM_MIN_BLOCKS
+#endif
 template <int MC>
 struct GmTraits {
   static constexpr bool big = false;
   static constexpr int min_blocks = PTYCHO_GM_MIN_BLOCKS;
+  static constexpr int threads = kGmThreads;
 };
 template <>
 struct GmTraits<256> {
   static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16;
   static constexpr int min_blocks = 2;
+  static constexpr int threads = kGmThreads;
 };
 template <>
 struct GmTraits<96> {
   static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16;
   static constexpr int min_blocks = 3;
+  static constexpr int threads = kGmThreads;
+};
+template <>
+struct GmTraits<192> {
+  static constexpr bool big = false;
+  static constexpr int min_blocks = PTYCHO_GM192_MIN_BLOCKS;
+  static constexpr int threads = PTYCHO_GM192_THREADS;
 };
 
 // Lines per block: the largest divisor of M with L M <= PTYCHO_GM_ELEMS.
@@ -361,7 +377,7 @@ __device__ __forceinline__ void gm_stage(const GmCtx<MC>& c, const float2* __res
                                          float2* __restrict__ dst, int Ns, int toff, bool cj, int t) {
   const int M = c.M(), L = c.L(), LS = gm_line_stride(M);
   const int nb = M / R;
-  for (int idx = t; idx < L * nb; idx += kGmThreads) {
+  for (int idx = t; idx < L * nb; idx += GmTraits<MC>::threads) {
     int li, j;
     if (c.g.cols) {
       j = idx / L;
@@ -483,7 +499,7 @@ __device__ __forceinline__ float2* gm_tf(const GmCtx<MC>& c, const GmPlan& plan,
 //                                at s = 0 into the probe-gradient workspace instead.
 // Skipped (out-of-range) windows carry zeros and flag the call.
 template <int MC>
-__global__ void __launch_bounds__(kGmThreads, GmTraits<MC>::min_blocks) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
+__global__ void __launch_bounds__(GmTraits<MC>::threads, GmTraits<MC>::min_blocks) k_gm_line(const ChainArgs a, float2* __restrict__ wv, int M, GmPlan plan,
                                                  GmLineArgs g) {
   if constexpr (MC > 0) M = MC;
   const int L = MC > 0 ? gm_lines(MC) : gm_lines(M);
@@ -501,7 +517,7 @@ __global__ void __launch_bounds__(kGmThreads, GmTraits<MC>::min_blocks) k_gm_lin
       const int R = MC > 0 ? gm_radix_at(MC, i, GmTraits<MC>::big) : plan.r[i];
       if (Ns > 1) {
         const int tstep = M / (Ns * R);
-        for (int e = t; e < (R - 1) * Ns; e += kGmThreads) {
+        for (int e = t; e < (R - 1) * Ns; e += GmTraits<MC>::threads) {
           const int q = 1 + e / Ns, k = e - (q - 1) * Ns;
           Tst[toff + e] = a.tw[tstep * q * k];
         }
@@ -509,7 +525,7 @@ __global__ void __launch_bounds__(kGmThreads, GmTraits<MC>::min_blocks) k_gm_lin
       }
       Ns *= R;
     }
-    for (int k = t; k < M; k += kGmThreads) Hs[k] = a.hs[k];
+    for (int k = t; k < M; k += GmTraits<MC>::threads) Hs[k] = a.hs[k];
   }
   const int g0 = blockIdx.x * L;  // first line of this block (L divides M)
   const int il = g0 / M;
@@ -652,9 +668,9 @@ struct GmLauncher {
     const unsigned grid = (unsigned)((size_t)a.n_pos * M / gm_lines(M));
     const size_t smem = gm_fft_smem_bytes(M);
     switch (M) {
-      case 96: k_gm_line<96><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
-      case 192: k_gm_line<192><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
-      case 256: k_gm_line<256><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
+      case 96: k_gm_line<96><<<grid, GmTraits<96>::threads, smem, st>>>(a, wv, M, plan, g); break;
+      case 192: k_gm_line<192><<<grid, GmTraits<192>::threads, smem, st>>>(a, wv, M, plan, g); break;
+      case 256: k_gm_line<256><<<grid, GmTraits<256>::threads, smem, st>>>(a, wv, M, plan, g); break;
       default: k_gm_line<0><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
     }
     ++launches;
