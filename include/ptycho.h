@@ -85,6 +85,14 @@ extern "C" {
 #define PTYCHO_FLAG_TIMING      2  /* record CUDA events around every kernel
                                       family on the call's stream; read them
                                       with ptycho_plan_timing() */
+#define PTYCHO_FLAG_SELFTEST_TIMEOUT 4 /* diagnostic, split precisions only: the
+                                      kernel issues no tensor-core work and
+                                      waits for it anyway, so its bounded wait
+                                      (about 1 s) expires, it releases tensor
+                                      memory and ptycho_plan_status reports
+                                      PTYCHO_ERR_TIMEOUT.  Exercises that path
+                                      without a GPU fault; results are
+                                      meaningless. */
 
 typedef struct {
   float re, im;

@@ -24,6 +24,7 @@ PTYCHO_BF16X3 = 1
 PTYCHO_FP16X3 = 2
 PTYCHO_FLAG_ASYNC_CHECK = 1
 PTYCHO_FLAG_TIMING = 2
+PTYCHO_FLAG_SELFTEST_TIMEOUT = 4
 PTYCHO_CKPT_AUTO = -1
 
 ERROR_NAMES = {

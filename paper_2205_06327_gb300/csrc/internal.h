@@ -39,6 +39,7 @@ struct ChainArgs {
   float2* psi_out;        // [N][M][M] or null (forward mode)
   float* int_out;         // [N][M][M] or null (forward mode)
   int* status;            // device error word (PTYCHO_ERR_POSITION on a bad window)
+  int selftest_timeout;   // PTYCHO_FLAG_SELFTEST_TIMEOUT: the split-product kernel issues no MMAs
 };
 
 // chain_kernels.cu

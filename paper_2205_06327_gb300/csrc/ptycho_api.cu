@@ -361,6 +361,7 @@ ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe,
   a.ws_gp = pl->ws_gp;
   a.loss_part = pl->loss_part;
   a.status = pl->d_status;
+  a.selftest_timeout = (pl->p.flags & PTYCHO_FLAG_SELFTEST_TIMEOUT) ? 1 : 0;
   return a;
 }
 

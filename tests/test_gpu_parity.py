@@ -422,6 +422,35 @@ def test_bf16x3_rejects_other_windows(dev):
 TOL_FP16X3 = 2e-4
 
 
+def test_split_product_wait_timeout_is_reported(dev):
+    """The split-product kernel's bounded wait on the tensor core: with
+    PTYCHO_FLAG_SELFTEST_TIMEOUT it issues no MMAs and waits anyway, so the
+    wait expires (about 1 s), the block releases tensor memory and returns,
+    and the plan's status reports PTYCHO_ERR_TIMEOUT.  The context stays
+    usable: a normal evaluation afterwards matches the oracle."""
+    import ctypes as C
+
+    from paper_2205_06327_gb300 import _lib
+    wl = synth.workload_random(128, 2, 1, 1, 9, seed=61)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    lib = _lib.load()
+    p = _lib.PtychoParams(M=wl.M, S=wl.S, H=wl.H, W=wl.W, N=wl.N, lambda_A=wl.lambda_A, dz_A=wl.dz_A,
+                          pixel_A=wl.pixel_A, precision=_lib.PTYCHO_FP16X3,
+                          flags=_lib.PTYCHO_FLAG_ASYNC_CHECK | _lib.PTYCHO_FLAG_SELFTEST_TIMEOUT)
+    h = C.c_void_p()
+    assert lib.ptycho_plan_create(C.byref(h), C.byref(p)) == _lib.PTYCHO_OK
+    pos, probe = to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev)
+    obj, meas = to_dev(wl.obj, torch.complex64, dev), to_dev(I, torch.float32, dev)
+    loss = torch.zeros((), dtype=torch.float64, device=dev)
+    rc = lib.ptycho_loss_grad(h, pos.data_ptr(), probe.data_ptr(), obj.data_ptr(), meas.data_ptr(),
+                              loss.data_ptr(), None, None, torch.cuda.current_stream(dev).cuda_stream)
+    assert rc == _lib.PTYCHO_OK
+    torch.cuda.synchronize()
+    assert lib.ptycho_plan_status(h) == _lib.PTYCHO_ERR_TIMEOUT
+    assert lib.ptycho_plan_destroy(h) == _lib.PTYCHO_OK
+    _check(wl, wl.obj, I, dev, tol=2e-4, precision="fp16x3")
+
+
 @pytest.mark.parametrize("S", [1, 5])
 def test_fp16x3_random_problems(dev, S):
     wl = synth.workload_random(128, S, 2, 3, 19, seed=70 + S, amp_jitter=0.15)
