@@ -126,9 +126,9 @@ typedef struct {
                          more FFT work.  L = 0 is used when L >= S.
                          PTYCHO_CKPT_AUTO: K = ceil(sqrt(S)) checkpoints,
                          L = ceil(S / K), which keeps about 2 sqrt(S) waves
-                         per position.  Recompute mode
-                         applies to the FP32 path with M = 64 or 128; the
-                         other paths keep every wave. */
+                         per position.  Recompute mode applies to the FP32
+                         path with M = 64 or 128; the other paths keep every
+                         wave. */
 } ptycho_params;
 
 #define PTYCHO_CKPT_AUTO (-1)  /* ptycho_params.ckpt_every: ceil(sqrt(S)) checkpoints */
@@ -148,8 +148,11 @@ PTYCHO_API int ptycho_plan_destroy(ptycho_plan plan);
 /* Number of positions processed per chunk and workspace bytes held. */
 PTYCHO_API int ptycho_plan_info(ptycho_plan plan, int32_t* chunk_positions, int64_t* workspace_bytes);
 
-/* Device-side status of the most recent call on this plan (after the stream
- * has been synchronised): PTYCHO_OK or PTYCHO_ERR_POSITION.  Clears it. */
+/* Device-side status of the calls on this plan since the last read (after
+ * the stream has been synchronised), and clears it: PTYCHO_OK,
+ * PTYCHO_ERR_POSITION (a window outside the object was skipped),
+ * PTYCHO_ERR_TIMEOUT (a bounded tensor-core wait gave up) or
+ * PTYCHO_ERR_UNSUPPORTED (a wave value left the FP16 range). */
 PTYCHO_API int ptycho_plan_status(ptycho_plan plan);
 
 /* Forward model G (Sec. II-B) for all N positions.
