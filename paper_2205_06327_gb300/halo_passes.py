@@ -17,6 +17,9 @@ On one GPU the library sums the gradient with the owner-computes tiled
 accumulation instead; this module runs the decomposition over any
 torch.distributed process group (gloo ranks on CPU in the tests), with
 non-blocking point-to-point messages as in the paper's asynchronous passes.
+:func:`appp_epoch` runs the paper's pipelined schedule (Alg. 2) on top of them:
+per-location updates of each extended tile, with the accumulated gradients
+reconciled every T locations.
 """
 from __future__ import annotations
 
@@ -140,6 +143,34 @@ def exchange(buf: torch.Tensor, grid, me: Tile, group=None) -> None:
     _pass(buf, grid, me, 0, False, rank_of, group)
     _pass(buf, grid, me, 1, True, rank_of, group)
     _pass(buf, grid, me, 1, False, rank_of, group)
+
+
+def appp_epoch(buf_tile: torch.Tensor, acc: torch.Tensor, grid, me: Tile, my_pos: np.ndarray, grad_fn,
+               alpha: float, T: int, group=None) -> None:
+    """One pass over this rank's probe locations of the paper's asynchronous
+    pipelined schedule (Alg. 2), in place on its extended tile ``buf_tile``
+    and its accumulated-gradient buffer ``acc`` (both [..., ext height, ext
+    width]; ``acc`` carries over between passes).  For the i-th location
+    (i = 1, 2, ...): its gradient g_i = grad_fn(index, buf_tile) (the tile's
+    shape, zero outside the window), acc += g_i, tile -= alpha g_i; after
+    every T-th location the four passes reconcile the buffers with the
+    neighbours (:func:`exchange`), the tile takes a second step
+    tile -= alpha acc, and acc is reset.  Ranks own different numbers of
+    locations, so i follows a count common to all ranks (the largest rank's):
+    a rank whose locations ran out still joins every exchange."""
+    n = len(my_pos)
+    cnt = torch.tensor([n], dtype=torch.int64)
+    dist.all_reduce(cnt, op=dist.ReduceOp.MAX, group=group)
+    n_max = int(cnt.item())
+    for i in range(1, n_max + 1):
+        if i <= n:
+            g = grad_fn(int(my_pos[i - 1]), buf_tile)
+            acc += g
+            buf_tile -= alpha * g
+        if i % T == 0:
+            exchange(acc, grid, me, group)
+            buf_tile -= alpha * acc
+            acc.zero_()
 
 
 def stitch(tiles_and_bufs, shape) -> torch.Tensor:

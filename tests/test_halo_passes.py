@@ -88,3 +88,115 @@ def test_stitching_the_cores_recovers_the_image():
             pieces.append((t, torch.from_numpy(gO[:, e.y0:e.y1, e.x0:e.x1].copy())))
     st = hp.stitch(pieces, gO.shape)
     assert np.array_equal(st.numpy(), gO)
+
+
+# ------------------------------------------------ Alg. 2: pipelined schedule with period T
+
+ALPHA = 2e-3
+
+
+def _grad_fn(wl, I, h, e):
+    """Location i's object gradient on the extended tile e (oracle, FP64)."""
+    def f(i, tile):
+        y, x = int(wl.pos[i][0]) - e.y0, int(wl.pos[i][1]) - e.x0
+        _, gOi, _ = orc.position_loss_grad(wl.probe, tile.numpy(), np.array([y, x]), I[i], h)
+        g = torch.zeros_like(tile)
+        g[:, y:y + wl.M, x:x + wl.M] = torch.from_numpy(gOi)
+        return g
+    return f
+
+
+def _owned(wl, grid, R, C):
+    from paper_2205_06327_gb300 import halo_passes as hp
+    ys = np.array([grid[r][0].core.y0 for r in range(R)] + [wl.H])
+    xs = np.array([grid[0][c].core.x0 for c in range(C)] + [wl.W])
+    return hp.assign_positions(wl.pos, wl.M, ys, xs)
+
+
+def _appp_worker(rank, world, R, C, T, epochs, port, out):
+    import torch.distributed as dist
+
+    from paper_2205_06327_gb300 import halo_passes as hp
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    wl, obj, I, h = _problem()
+    grid = hp.tile_grid(wl.H, wl.W, R, C, wl.pos, wl.M)
+    me = grid[rank // C][rank % C]
+    e = me.ext
+    mine = np.nonzero(_owned(wl, grid, R, C) == rank)[0]
+    tile = torch.from_numpy(obj[:, e.y0:e.y1, e.x0:e.x1].copy())
+    acc = torch.zeros_like(tile)
+    for _ in range(epochs):
+        hp.appp_epoch(tile, acc, grid, me, mine, _grad_fn(wl, I, h, e), ALPHA, T)
+    out[rank] = tile.numpy()
+    dist.destroy_process_group()
+
+
+def _appp_reference(R, C, T, epochs):
+    """The same schedule in one process: every tile's own loop, and at each
+    common exchange point the global sum of all buffers, restricted to each
+    extended tile (what the four passes deliver, tested above)."""
+    from paper_2205_06327_gb300 import halo_passes as hp
+    wl, obj, I, h = _problem()
+    grid = hp.tile_grid(wl.H, wl.W, R, C, wl.pos, wl.M)
+    owner = _owned(wl, grid, R, C)
+    tiles = [t for row in grid for t in row]
+    mine = [np.nonzero(owner == k)[0] for k in range(len(tiles))]
+    V = [torch.from_numpy(obj[:, t.ext.y0:t.ext.y1, t.ext.x0:t.ext.x1].copy()) for t in tiles]
+    acc = [torch.zeros_like(v) for v in V]
+    n_max = max(len(m) for m in mine)
+    for _ in range(epochs):
+        for i in range(1, n_max + 1):
+            for k, t in enumerate(tiles):
+                if i <= len(mine[k]):
+                    g = _grad_fn(wl, I, h, t.ext)(int(mine[k][i - 1]), V[k])
+                    acc[k] += g
+                    V[k] -= ALPHA * g
+            if i % T == 0:
+                G = torch.zeros(obj.shape, dtype=torch.complex128)
+                for k, t in enumerate(tiles):
+                    G[:, t.ext.y0:t.ext.y1, t.ext.x0:t.ext.x1] += acc[k]
+                for k, t in enumerate(tiles):
+                    V[k] -= ALPHA * G[:, t.ext.y0:t.ext.y1, t.ext.x0:t.ext.x1]
+                    acc[k].zero_()
+    return [v.numpy() for v in V]
+
+
+@pytest.mark.parametrize("R,C,T,epochs", [(2, 2, 3, 2), (2, 2, 1000, 1), (1, 3, 5, 1)])
+def test_appp_schedule_matches_the_reconciled_reference(R, C, T, epochs):
+    """Alg. 2 on gloo ranks: per-location updates of each extended tile, the
+    buffers reconciled by the passes every T locations (T = 1000: once, after
+    the largest rank's last location), then the second update."""
+    world = R * C
+    manager = mp.Manager()
+    out = manager.dict()
+    mp.spawn(_appp_worker, args=(world, R, C, T, epochs, _free_port(), out), nprocs=world, join=True)
+    ref = _appp_reference(R, C, T, epochs)
+    for k in range(world):
+        scale = np.abs(ref[k]).max()
+        assert np.abs(out[k] - ref[k]).max() <= 1e-12 * scale, k
+
+
+def test_appp_single_tile_period_one_is_sgd_with_twice_the_step():
+    """One tile, T = 1: the pass has no neighbour, so each location's gradient
+    is applied twice, i.e. plain per-location descent with step 2 alpha."""
+    import torch.distributed as dist
+
+    from paper_2205_06327_gb300 import halo_passes as hp
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()))
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        wl, obj, I, h = _problem()
+        grid = hp.tile_grid(wl.H, wl.W, 1, 1, wl.pos, wl.M)
+        me = grid[0][0]
+        e = me.ext
+        f = _grad_fn(wl, I, h, e)
+        tile = torch.from_numpy(obj[:, e.y0:e.y1, e.x0:e.x1].copy())
+        order = np.arange(wl.N)
+        hp.appp_epoch(tile, torch.zeros_like(tile), grid, me, order, f, ALPHA, 1)
+        ref = torch.from_numpy(obj[:, e.y0:e.y1, e.x0:e.x1].copy())
+        for i in order:
+            ref -= 2 * ALPHA * f(int(i), ref)
+        assert np.abs(tile.numpy() - ref.numpy()).max() <= 1e-12 * np.abs(ref.numpy()).max()
+    finally:
+        dist.destroy_process_group()
