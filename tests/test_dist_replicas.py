@@ -35,7 +35,7 @@ def _worker(rank, world, port, out):
 def test_two_rank_replicas_report_max_time():
     world = 2
     port = _free_port()
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()
     out = manager.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     assert out[0] == out[1] == 2.0

@@ -63,7 +63,7 @@ def _worker(rank, world, R, C, port, out):
 @pytest.mark.parametrize("R,C", [(2, 2), (3, 3), (1, 3)])
 def test_passes_give_the_global_gradient_on_every_extended_tile(R, C):
     world = R * C
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()
     out = manager.dict()
     mp.spawn(_worker, args=(world, R, C, _free_port(), out), nprocs=world, join=True)
     wl, _, _, _ = _problem()
@@ -168,7 +168,7 @@ def test_appp_schedule_matches_the_reconciled_reference(R, C, T, epochs):
     buffers reconciled by the passes every T locations (T = 1000: once, after
     the largest rank's last location), then the second update."""
     world = R * C
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()
     out = manager.dict()
     mp.spawn(_appp_worker, args=(world, R, C, T, epochs, _free_port(), out), nprocs=world, join=True)
     ref = _appp_reference(R, C, T, epochs)
