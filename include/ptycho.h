@@ -179,6 +179,27 @@ PTYCHO_API int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const p
                      const ptycho_c64* obj, const float* meas_I, double* loss_out,
                      ptycho_c64* grad_obj, ptycho_c64* grad_probe, void* stream);
 
+/* ptycho_loss_grad with every array in HOST memory, for callers whose data
+ * live on the host.  Same operation (Eq. 1, Eq. 2), arguments, layouts and
+ * results bit for bit; the call is synchronous: it returns when loss_out,
+ * grad_obj and grad_probe hold the results.
+ *   pos_yx, probe, obj, meas_I   host inputs (layouts as above).  Pinned
+ *       memory (cudaHostAlloc, or PyTorch's pin_memory) lets the uploads
+ *       run beside the kernels; pageable memory works with plain copies.
+ *   loss_out   double[1] host (required)
+ *   grad_obj, grad_probe   host outputs, or NULL
+ * The plan keeps device copies of the inputs and gradients (allocated on the
+ * first call: (N M^2 4 + 2 S H W 8 + 2 M^2 8 + N 8) bytes) and a copy
+ * stream.  Positions are checked on the host before any upload.  The object
+ * and the first chain wave's intensities go up on `stream`; the other
+ * intensities go up on the copy stream while that wave runs, and the chain of
+ * the later positions waits for them.  Errors as for ptycho_loss_grad, and
+ * PTYCHO_ERR_ARG when an array is a device pointer.  The paper has no
+ * counterpart: it is a packaging of the same kernels. */
+PTYCHO_API int ptycho_loss_grad_host(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe,
+                     const ptycho_c64* obj, const float* meas_I, double* loss_out,
+                     ptycho_c64* grad_obj, ptycho_c64* grad_probe, void* stream);
+
 /* One full-batch gradient-descent step (Sec. II-B update rule, applied to the
  * position sum of Eq. 2): O <- O - t alpha_obj dF/dO, P <- P - t alpha_probe dF/dP,
  * in place.  line_search = 0: t = 1.  line_search = 1: Armijo backtracking,

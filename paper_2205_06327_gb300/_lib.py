@@ -39,7 +39,8 @@ ERROR_NAMES = {
 # Every symbol include/ptycho.h declares.
 EXPORTED = [
     "ptycho_plan_create", "ptycho_plan_destroy", "ptycho_plan_info", "ptycho_plan_status",
-    "ptycho_forward", "ptycho_loss_grad", "ptycho_step", "ptycho_plan_timing", "ptycho_loss_grad_noalloc",
+    "ptycho_forward", "ptycho_loss_grad", "ptycho_loss_grad_host", "ptycho_step", "ptycho_plan_timing",
+    "ptycho_loss_grad_noalloc",
     "ptycho_potential_to_transmission", "ptycho_potential_grad", "ptycho_last_error", "ptycho_version",
     "ptycho_multi_loss_grad", "ptycho_multi_step",
 ]
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ptycho_plan_status": ([vp], C.c_int),
         "ptycho_forward": ([vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_loss_grad": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "ptycho_loss_grad_host": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_step": ([vp, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp], C.c_int),
         "ptycho_plan_timing": ([vp, C.POINTER(PtychoTiming), i32], C.c_int),
         "ptycho_loss_grad_noalloc": ([C.POINTER(PtychoParams), vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),

@@ -160,9 +160,14 @@ class Plan:
 
     def loss_grad(self, pos, probe, obj, meas, want_obj: bool = True, want_probe: bool = True,
                   out_obj: torch.Tensor | None = None, out_probe: torch.Tensor | None = None):
-        """(F, dF/dO, dF/dP) of Eq. 1 / Eq. 2.  F is a float64 0-d tensor on the device."""
+        """(F, dF/dO, dF/dP) of Eq. 1 / Eq. 2.  F is a float64 0-d tensor on the device.
+
+        With every input on the host the call goes through ptycho_loss_grad_host
+        (uploads overlapped with the chain) and returns host tensors."""
         host = not probe.is_cuda
         g = self.geom
+        if all(not t.is_cuda for t in (pos, probe, obj, meas)):
+            return self._loss_grad_host(pos, probe, obj, meas, want_obj, want_probe, out_obj, out_probe)
         pos, probe, obj, meas = self._inputs(pos, probe, obj, meas)
         gO = out_obj if out_obj is not None else (
             torch.empty((g.S, g.H, g.W), dtype=torch.complex64, device=self.device) if want_obj else None)
@@ -175,6 +180,35 @@ class Plan:
         if host:
             with torch.cuda.device(self.device):
                 loss, gO, gP = self._to_host(loss, gO, gP)
+        return loss, gO, gP
+
+    def _loss_grad_host(self, pos, probe, obj, meas, want_obj, want_probe, out_obj, out_probe):
+        g = self.geom
+
+        def inp(t, dtype, shape, name):
+            if t.dtype != dtype:
+                raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+            if tuple(t.shape) != tuple(shape):
+                raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+            return t.contiguous()
+
+        def out(t, shape, name, want):
+            if t is None:
+                return torch.empty(shape, dtype=torch.complex64, pin_memory=True) if want else None
+            if t.is_cuda or t.dtype != torch.complex64 or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex64 host tensor of shape {tuple(shape)}")
+            return t
+
+        pos = inp(pos, torch.int32, (g.N, 2), "pos")
+        probe = inp(probe, torch.complex64, (g.M, g.M), "probe")
+        obj = inp(obj, torch.complex64, (g.S, g.H, g.W), "obj")
+        meas = inp(meas, torch.float32, (g.N, g.M, g.M), "meas")
+        gO = out(out_obj, (g.S, g.H, g.W), "out_obj", want_obj)
+        gP = out(out_probe, (g.M, g.M), "out_probe", want_probe)
+        loss = torch.empty((), dtype=torch.float64)
+        with torch.cuda.device(self.device):
+            check(self.lib.ptycho_loss_grad_host(self._h, _ptr(pos), _ptr(probe), _ptr(obj), _ptr(meas),
+                                                 _ptr(loss), _ptr(gO), _ptr(gP), _stream_handle(self.device)))
         return loss, gO, gP
 
     def step(self, pos, probe: torch.Tensor, obj: torch.Tensor, meas, alpha_obj: float, alpha_probe: float,

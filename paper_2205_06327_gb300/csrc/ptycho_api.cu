@@ -199,6 +199,17 @@ struct ptycho_plan_s {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int wave = 0;               // chain blocks resident on the whole GPU at once
+  // host-buffer entry point (allocated on first use): device copies of the
+  // inputs and gradients, and a copy stream that uploads the intensities of
+  // all but the first chain wave while that wave runs
+  int32_t* x_pos = nullptr;
+  float2* x_probe = nullptr;
+  float2* x_obj = nullptr;
+  float* x_meas = nullptr;
+  float2* x_gO = nullptr;
+  float2* x_gP = nullptr;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_first = nullptr, ev_rest = nullptr;
   struct Mark {
     int kind;
     cudaEvent_t start, stop;
@@ -233,6 +244,15 @@ void free_plan(ptycho_plan pl) {
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
   if (pl->ev_join) cudaEventDestroy(pl->ev_join);
   if (pl->side) cudaStreamDestroy(pl->side);
+  cudaFree(pl->x_pos);
+  cudaFree(pl->x_probe);
+  cudaFree(pl->x_obj);
+  cudaFree(pl->x_meas);
+  cudaFree(pl->x_gO);
+  cudaFree(pl->x_gP);
+  if (pl->ev_first) cudaEventDestroy(pl->ev_first);
+  if (pl->ev_rest) cudaEventDestroy(pl->ev_rest);
+  if (pl->copy) cudaStreamDestroy(pl->copy);
   if (pl->h_pos) cudaFreeHost(pl->h_pos);
   if (pl->h_scal) cudaFreeHost(pl->h_scal);
   delete pl;
@@ -279,6 +299,8 @@ int validate_params(const ptycho_params& p) {
   return PTYCHO_OK;
 }
 
+int check_windows(const ptycho_params& p, const int32_t* h_pos);
+
 // Positions check on the host (pinned copy) unless the plan asks for the
 // asynchronous device-side check only.
 int check_positions(ptycho_plan pl, const int32_t* pos, cudaStream_t st) {
@@ -289,8 +311,13 @@ int check_positions(ptycho_plan pl, const int32_t* pos, cudaStream_t st) {
   if (p.flags & PTYCHO_FLAG_ASYNC_CHECK) return PTYCHO_OK;
   CUDA_TRY(cudaMemcpyAsync(pl->h_pos, pos, sizeof(int32_t) * 2 * (size_t)p.N, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  return check_windows(p, pl->h_pos);
+}
+
+// Every window inside the object: 0 <= y <= H - M, 0 <= x <= W - M.
+int check_windows(const ptycho_params& p, const int32_t* h_pos) {
   for (int i = 0; i < p.N; ++i) {
-    const int y = pl->h_pos[2 * i], x = pl->h_pos[2 * i + 1];
+    const int y = h_pos[2 * i], x = h_pos[2 * i + 1];
     if (y < 0 || x < 0 || y > p.H - p.M || x > p.W - p.M) {
       char buf[160];
       snprintf(buf, sizeof buf, "position %d (y=%d, x=%d) puts the %dx%d window outside the %dx%d object", i, y, x,
@@ -366,10 +393,13 @@ ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe,
 }
 
 // F (and optionally gradients) at (probe + probe_step*probe_dir, obj + obj_step*obj_dir);
-// the loss lands in pl->d_scal[slot].
+// the loss lands in pl->d_scal[slot].  With rest_ready, only the intensities
+// of the first n_first positions are ready when the call starts: the chain of
+// those positions is launched first, then st waits for rest_ready.
 int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, const ptycho_c64* obj,
                   const float* meas, float2* grad_obj, float2* grad_probe, int slot, const float2* obj_dir,
-                  float obj_step, const float2* probe_dir, float probe_step, cudaStream_t st) {
+                  float obj_step, const float2* probe_dir, float probe_step, cudaStream_t st,
+                  int n_first = 0, cudaEvent_t rest_ready = nullptr) {
   const ptycho_params& p = pl->p;
   const bool want_grad = grad_obj || grad_probe;
   if (p.N == 0) {
@@ -385,6 +415,17 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
   a.probe_step = probe_step;
   const ChainMode mode = !want_grad ? MODE_LOSS : (pl->ckpt_L ? MODE_GRAD_RC : MODE_GRAD);
   const size_t MM = (size_t)p.M * p.M;
+  // Positions [off, off + n) of the current chunk (workspace slots from off).
+  auto sub = [&](const ChainArgs& ca, int off, int n) {
+    ChainArgs r = ca;
+    r.pos_begin = ca.pos_begin + off;
+    r.n_pos = n;
+    r.ws_psi = pl->ws_psi + (size_t)off * MM;
+    r.ws_gphi = pl->ws_gphi + (size_t)off * MM;
+    r.ws_gp = pl->ws_gp + (size_t)off * MM;
+    r.loss_part = pl->loss_part + off;
+    return r;
+  };
   auto launch_chain_for = [&](const ChainArgs& ca) -> int {
     int gm_launches = 0;
     if (pl->wv) {
@@ -433,18 +474,18 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     const int n1 = n - tail;
     a.pos_begin = c0;
     a.n_pos = n1;
-    int rc = launch_chain_for(a);
-    if (rc) return rc;
+    int rc;
+    if (rest_ready && ci == 0) {
+      const int nf = n_first < n1 ? n_first : n1;
+      if ((rc = launch_chain_for(sub(a, 0, nf))) != PTYCHO_OK) return rc;
+      CUDA_TRY(cudaStreamWaitEvent(st, rest_ready, 0));
+      if (n1 > nf && (rc = launch_chain_for(sub(a, nf, n1 - nf))) != PTYCHO_OK) return rc;
+    } else if ((rc = launch_chain_for(a)) != PTYCHO_OK) {
+      return rc;
+    }
     if (tail) {
       CUDA_TRY(cudaEventRecord(pl->ev_fork, st));
-      ChainArgs at = a;
-      at.pos_begin = c0 + n1;
-      at.n_pos = tail;
-      at.ws_psi = pl->ws_psi + (size_t)n1 * MM;
-      at.ws_gphi = pl->ws_gphi + (size_t)n1 * MM;
-      at.ws_gp = pl->ws_gp + (size_t)n1 * MM;
-      at.loss_part = pl->loss_part + n1;
-      if ((rc = launch_chain_for(at)) != PTYCHO_OK) return rc;
+      if ((rc = launch_chain_for(sub(a, n1, tail))) != PTYCHO_OK) return rc;
       CUDA_TRY(cudaStreamWaitEvent(pl->side, pl->ev_fork, 0));
       if ((rc = accum_for(c0, 0, n1, ci > 0, pl->side)) != PTYCHO_OK) return rc;
       CUDA_TRY(cudaEventRecord(pl->ev_join, pl->side));
@@ -787,9 +828,100 @@ int run_multi(const ptycho_problem* probs, int32_t n, F&& fn) {
   return PTYCHO_OK;
 }
 
+// ptycho_loss_grad_host: host arrays in and out.  The inputs are staged in
+// plan-owned device buffers; the intensities of all but the first chain wave
+// go up on the copy stream while that wave runs.
+int loss_grad_host_impl(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
+                        const float* meas_I, double* loss_out, ptycho_c64* grad_obj, ptycho_c64* grad_probe,
+                        cudaStream_t st) {
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  ptycho_plan pl = plan;
+  const ptycho_params& p = pl->p;
+  struct Arg {
+    const void* ptr;
+    const char* name;
+    bool required;
+  } args[] = {{pos_yx, "pos_yx", p.N > 0}, {probe, "probe", true},           {obj, "obj", true},
+              {meas_I, "meas_I", p.N > 0}, {loss_out, "loss_out", true},      {grad_obj, "grad_obj", false},
+              {grad_probe, "grad_probe", false}};
+  for (const Arg& x : args) {
+    if (!x.ptr) {
+      if (x.required) return fail(PTYCHO_ERR_ARG, std::string(x.name) + " is NULL");
+      continue;
+    }
+    if (is_device_ptr(x.ptr)) return fail(PTYCHO_ERR_ARG, std::string(x.name) + " must be a host pointer");
+  }
+  int rc;
+  if (p.N > 0 && (rc = check_windows(p, pos_yx))) return rc;
+
+  const size_t MM = (size_t)p.M * p.M, nO = (size_t)p.S * p.H * p.W;
+  if (!pl->x_probe) {
+    rc = PTYCHO_OK;
+    if (!rc) rc = dev_alloc(&pl->x_pos, 2 * (size_t)p.N, "staged positions");
+    if (!rc) rc = dev_alloc(&pl->x_probe, MM, "staged probe");
+    if (!rc) rc = dev_alloc(&pl->x_obj, nO, "staged object");
+    if (!rc) rc = dev_alloc(&pl->x_meas, (size_t)p.N * MM, "staged intensities");
+    if (!rc) rc = dev_alloc(&pl->x_gO, nO, "staged object gradient");
+    if (!rc) rc = dev_alloc(&pl->x_gP, MM, "staged probe gradient");
+    cudaError_t e;
+    if (!rc && ((e = cudaStreamCreateWithFlags(&pl->copy, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&pl->ev_first, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&pl->ev_rest, cudaEventDisableTiming)) != cudaSuccess))
+      rc = cuda_fail(e, "copy stream");
+    if (rc) {  // leave nothing half-made: the next call starts over
+      cudaFree(pl->x_pos); cudaFree(pl->x_probe); cudaFree(pl->x_obj);
+      cudaFree(pl->x_meas); cudaFree(pl->x_gO); cudaFree(pl->x_gP);
+      pl->x_pos = nullptr; pl->x_probe = pl->x_obj = pl->x_gO = pl->x_gP = nullptr; pl->x_meas = nullptr;
+      if (pl->ev_first) cudaEventDestroy(pl->ev_first);
+      if (pl->ev_rest) cudaEventDestroy(pl->ev_rest);
+      if (pl->copy) cudaStreamDestroy(pl->copy);
+      pl->ev_first = pl->ev_rest = nullptr;
+      pl->copy = nullptr;
+      return rc;
+    }
+  }
+  // Uploads in the order the chain needs them.  The copy stream starts after
+  // the first part is up, so the two parts do not share the link, and after
+  // everything earlier on st (a previous call still reading the buffers).
+  const int n_first = pl->wave > 0 && pl->wave < p.N ? pl->wave : p.N;
+  if (p.N > 0)
+    CUDA_TRY(cudaMemcpyAsync(pl->x_pos, pos_yx, sizeof(int32_t) * 2 * (size_t)p.N, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(pl->x_probe, probe, sizeof(float2) * MM, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(pl->x_obj, obj, sizeof(float2) * nO, cudaMemcpyHostToDevice, st));
+  if (p.N > 0)
+    CUDA_TRY(cudaMemcpyAsync(pl->x_meas, meas_I, sizeof(float) * MM * (size_t)n_first, cudaMemcpyHostToDevice, st));
+  cudaEvent_t rest = nullptr;
+  if (n_first < p.N) {
+    CUDA_TRY(cudaEventRecord(pl->ev_first, st));
+    CUDA_TRY(cudaStreamWaitEvent(pl->copy, pl->ev_first, 0));
+    CUDA_TRY(cudaMemcpyAsync(pl->x_meas + MM * (size_t)n_first, meas_I + MM * (size_t)n_first,
+                             sizeof(float) * MM * (size_t)(p.N - n_first), cudaMemcpyHostToDevice, pl->copy));
+    CUDA_TRY(cudaEventRecord(pl->ev_rest, pl->copy));
+    rest = pl->ev_rest;
+  }
+  rc = run_loss_grad(pl, pl->x_pos, reinterpret_cast<const ptycho_c64*>(pl->x_probe),
+                     reinterpret_cast<const ptycho_c64*>(pl->x_obj), pl->x_meas, grad_obj ? pl->x_gO : nullptr,
+                     grad_probe ? pl->x_gP : nullptr, 0, nullptr, 0.f, nullptr, 0.f, st, n_first, rest);
+  if (rc) {
+    cudaStreamSynchronize(pl->copy);  // no upload left running into the buffers
+    return rc;
+  }
+  if (grad_obj) CUDA_TRY(cudaMemcpyAsync(grad_obj, pl->x_gO, sizeof(float2) * nO, cudaMemcpyDeviceToHost, st));
+  if (grad_probe) CUDA_TRY(cudaMemcpyAsync(grad_probe, pl->x_gP, sizeof(float2) * MM, cudaMemcpyDeviceToHost, st));
+  return deliver_loss(pl, 0, loss_out, st);  // synchronises st
+}
+
 }  // namespace
 
 extern "C" {
+
+int ptycho_loss_grad_host(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
+                          const float* meas_I, double* loss_out, ptycho_c64* grad_obj, ptycho_c64* grad_probe,
+                          void* stream) {
+  g_last_error.clear();
+  return loss_grad_host_impl(plan, pos_yx, probe, obj, meas_I, loss_out, grad_obj, grad_probe,
+                             static_cast<cudaStream_t>(stream));
+}
 
 int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe, const ptycho_c64* obj,
                      const float* meas_I, double* loss_out, ptycho_c64* grad_obj, ptycho_c64* grad_probe,
