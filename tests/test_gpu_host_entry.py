@@ -33,14 +33,19 @@ def _host(a, dtype, pinned):
     return t.pin_memory() if pinned else t
 
 
-def _compare(dev, wl, obj, I, pinned=True, **plan_kw):
-    """Host entry vs device entry on one plan each; returns the host results."""
+def _compare(dev, wl, obj, I, pinned=True, pageable_out=False, **plan_kw):
+    """Host entry vs device entry on one plan each; returns the host results
+    (outputs in pinned host tensors, or in caller-given pageable ones)."""
     from paper_2205_06327_gb300 import api
     g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
     ph = api.Plan(g, dev, **plan_kw)
     pd = api.Plan(g, dev, **plan_kw)
+    outs = {}
+    if pageable_out:
+        outs = dict(out_obj=torch.empty((wl.S, wl.H, wl.W), dtype=torch.complex64),
+                    out_probe=torch.empty((wl.M, wl.M), dtype=torch.complex64))
     hl, hO, hP = ph.loss_grad(_host(wl.pos, torch.int32, pinned), _host(wl.probe, torch.complex64, pinned),
-                              _host(obj, torch.complex64, pinned), _host(I, torch.float32, pinned))
+                              _host(obj, torch.complex64, pinned), _host(I, torch.float32, pinned), **outs)
     assert not hO.is_cuda and not hP.is_cuda and not hl.is_cuda
     dl, dO, dP = pd.loss_grad(to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev),
                               to_dev(obj, torch.complex64, dev), to_dev(I, torch.float32, dev))
@@ -67,6 +72,8 @@ def test_host_entry_split_waves_matches_device_and_oracle(dev):
 def test_host_entry_pageable_inputs(dev):
     wl, obj, I = _case(128, 2, 14, 12, 9, 902)
     _compare(dev, wl, obj, I, pinned=False)
+    _compare(dev, wl, obj, I, pinned=False, pageable_out=True)
+    _compare(dev, wl, obj, I, pinned=True, pageable_out=True)
 
 
 def test_host_entry_several_chunks(dev):
