@@ -349,6 +349,8 @@ def run_gpu(args, world, rank, local, pool):
     wl = workload_for(args.config)
     if args.positions:
         wl.pos = wl.pos[: args.positions]
+    if args.order == "shuffled":
+        wl.pos = wl.pos[np.random.default_rng(12345).permutation(len(wl.pos))]
     obj0 = start_object(wl)
     geom = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
     tile = (0, 0)
@@ -494,7 +496,7 @@ def run_gpu(args, world, rank, local, pool):
         "config": {"workload": wl.name, "positions": wl.N, "M": wl.M, "S": wl.S, "object": [wl.H, wl.W],
                    "tiles": list(tile) if tile != (0, 0) else [32, 32],
                    "l2": "flushed between timed steps (512 MiB write, outside the step events)",
-                   "replicas": world, "wall_s": wall, "ckpt_every": args.ckpt_every,
+                   "replicas": world, "wall_s": wall, "ckpt_every": args.ckpt_every, "order": args.order,
                    "workspace_bytes": plan.workspace_bytes, "chunk": plan.chunk},
         "roofline": {"bound": bound, "kernel": "k_chain (slice chain, gradient mode)"
                      if args.precision == "fp32" else "k_chain_tc (split DFT products, gradient mode)",
@@ -625,6 +627,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=576)
     ap.add_argument("--positions", type=int, default=0, help="first N positions only (profiling cases)")
+    ap.add_argument("--order", default="raster", choices=["raster", "shuffled"],
+                    help="GPU legs: positions in the workload's raster order, or a seeded random permutation "
+                         "(the library uses the caller's order; this measures what the order costs)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "fp16x3"],
                     help="bf16x3 / fp16x3: 2-D transforms as hi/lo split DFT products on the tensor cores")
     ap.add_argument("--ckpt-every", type=int, default=None,
