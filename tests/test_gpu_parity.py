@@ -187,6 +187,25 @@ def test_window_at_object_corners(dev):
     _check(wl, start_object(wl, "perturbed", 4), I, dev)
 
 
+@pytest.mark.parametrize("M", [64, 128])
+def test_repeated_and_unsorted_positions(dev, M):
+    # The same window twice (both terms are summed, Eq. 2) and the positions in
+    # a seeded random order (the library keeps the caller's order): the
+    # oracle's sum over the same list.
+    wl = synth.workload_random(M, 3, 3, 4, 9, seed=15 + M, amp_jitter=0.1)
+    rep = np.concatenate([wl.pos, wl.pos[[1, 5, 5]]])
+    wl.pos = rep[np.random.default_rng(16).permutation(len(rep))].astype(np.int32)
+    I = (measurements(wl) * 0.9).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 6), I, dev)
+
+
+def test_single_position(dev):
+    wl = synth.workload_random(128, 4, 1, 1, 1, seed=17, amp_jitter=0.1)
+    wl.pos = np.array([[wl.H - wl.M - 1, wl.W - wl.M]], np.int32)  # off the raster, at the right edge
+    I = (measurements(wl) * 1.3).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", 7), I, dev)
+
+
 def test_zero_positions(dev):
     wl = synth.workload_random(64, 2, 1, 1, 1, seed=14)
     wl.pos = np.zeros((0, 2), np.int32)
