@@ -189,6 +189,7 @@ struct ptycho_plan_s {
   int* d_status = nullptr;
   int* h_pos = nullptr;       // pinned, [N][2]
   double* h_scal = nullptr;   // pinned, [8]
+  int* h_flag = nullptr;      // pinned, [1]: the device error word, read by the synchronous calls
   // gradient-descent step buffers (allocated on first use)
   float2* g_obj = nullptr;
   float2* g_probe = nullptr;
@@ -255,6 +256,7 @@ void free_plan(ptycho_plan pl) {
   if (pl->copy) cudaStreamDestroy(pl->copy);
   if (pl->h_pos) cudaFreeHost(pl->h_pos);
   if (pl->h_scal) cudaFreeHost(pl->h_scal);
+  if (pl->h_flag) cudaFreeHost(pl->h_flag);
   delete pl;
 }
 
@@ -300,6 +302,13 @@ int validate_params(const ptycho_params& p) {
 }
 
 int check_windows(const ptycho_params& p, const int32_t* h_pos);
+
+// The error a non-zero device error word stands for.
+int status_fail(int h) {
+  if (h == PTYCHO_ERR_TIMEOUT) return fail(h, "a bounded tensor-core wait gave up on the device");
+  if (h == PTYCHO_ERR_UNSUPPORTED) return fail(h, "a wave value left the FP16 range (|x| >= 60000)");
+  return fail(h, "a probe window outside the object was skipped on the device");
+}
 
 // Positions check on the host (pinned copy) unless the plan asks for the
 // asynchronous device-side check only.
@@ -628,7 +637,8 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
     return cuda_fail(e, "plane upload");
   }
   if (cudaMallocHost(&pl->h_pos, sizeof(int32_t) * 2 * (size_t)n) != cudaSuccess ||
-      cudaMallocHost(&pl->h_scal, sizeof(double) * 8) != cudaSuccess) {
+      cudaMallocHost(&pl->h_scal, sizeof(double) * 8) != cudaSuccess ||
+      cudaMallocHost(&pl->h_flag, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     free_plan(pl);
     return fail(PTYCHO_ERR_NOMEM, "pinned host allocation failed");
@@ -665,10 +675,7 @@ int ptycho_plan_status(ptycho_plan plan) {
   int h = 0;
   CUDA_TRY(cudaMemcpy(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(plan->d_status, 0, sizeof(int)));
-  if (h == PTYCHO_ERR_TIMEOUT) return fail(h, "a bounded tensor-core wait gave up on the device");
-  if (h == PTYCHO_ERR_UNSUPPORTED) return fail(h, "a wave value left the FP16 range (|x| >= 60000)");
-  if (h) return fail(h, "a probe window outside the object was skipped on the device");
-  return PTYCHO_OK;
+  return h ? status_fail(h) : PTYCHO_OK;
 }
 
 int ptycho_plan_timing(ptycho_plan plan, ptycho_timing* out, int32_t reset) {
@@ -908,7 +915,15 @@ int loss_grad_host_impl(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c6
   }
   if (grad_obj) CUDA_TRY(cudaMemcpyAsync(grad_obj, pl->x_gO, sizeof(float2) * nO, cudaMemcpyDeviceToHost, st));
   if (grad_probe) CUDA_TRY(cudaMemcpyAsync(grad_probe, pl->x_gP, sizeof(float2) * MM, cudaMemcpyDeviceToHost, st));
-  return deliver_loss(pl, 0, loss_out, st);  // synchronises st
+  // The call is synchronous, so it reports the device error word itself.
+  CUDA_TRY(cudaMemcpyAsync(pl->h_flag, pl->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if ((rc = deliver_loss(pl, 0, loss_out, st))) return rc;  // synchronises st
+  if (const int h = *pl->h_flag) {
+    CUDA_TRY(cudaMemsetAsync(pl->d_status, 0, sizeof(int), st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return status_fail(h);
+  }
+  return PTYCHO_OK;
 }
 
 }  // namespace

@@ -160,3 +160,30 @@ def test_host_entry_no_positions(dev):
                                 _host(obj, torch.complex64, True), torch.zeros((0, 64, 64), dtype=torch.float32))
     assert float(l0) == 0.0 and not gO.abs().any() and not gP.abs().any()
     plan.close()
+
+
+def test_host_entry_reports_a_device_timeout(dev):
+    """The synchronous host-buffer call reads the device error word itself:
+    the split-product kernel's self-test wait (no MMAs issued, the bounded
+    wait expires after about 1 s) comes back as PTYCHO_ERR_TIMEOUT from the
+    call, the word is cleared, and the next plain evaluation is correct."""
+    import ctypes as C
+
+    from paper_2205_06327_gb300 import _lib
+    wl, obj, I = _case(128, 2, 1, 1, 9, 910)
+    lib = _lib.load()
+    p = _lib.PtychoParams(M=wl.M, S=wl.S, H=wl.H, W=wl.W, N=wl.N, lambda_A=wl.lambda_A, dz_A=wl.dz_A,
+                          pixel_A=wl.pixel_A, precision=_lib.PTYCHO_FP16X3,
+                          flags=_lib.PTYCHO_FLAG_SELFTEST_TIMEOUT)
+    h = C.c_void_p()
+    assert lib.ptycho_plan_create(C.byref(h), C.byref(p)) == _lib.PTYCHO_OK
+    pos, probe = _host(wl.pos, torch.int32, True), _host(wl.probe, torch.complex64, True)
+    o, Ih = _host(obj, torch.complex64, True), _host(I, torch.float32, True)
+    loss = C.c_double(0.0)
+    with torch.cuda.device(dev):
+        rc = lib.ptycho_loss_grad_host(h, pos.data_ptr(), probe.data_ptr(), o.data_ptr(), Ih.data_ptr(),
+                                       C.addressof(loss), None, None, torch.cuda.current_stream(dev).cuda_stream)
+    assert rc == _lib.PTYCHO_ERR_TIMEOUT and b"gave up" in lib.ptycho_last_error()
+    assert lib.ptycho_plan_status(h) == _lib.PTYCHO_OK  # cleared by the call
+    assert lib.ptycho_plan_destroy(h) == _lib.PTYCHO_OK
+    _compare(dev, wl, obj, I, precision="fp16x3")
