@@ -194,10 +194,11 @@ PTYCHO_API int ptycho_loss_grad(ptycho_plan plan, const int32_t* pos_yx, const p
  * and the first chain wave's intensities go up on `stream`; the other
  * intensities go up on the copy stream while that wave runs, and the chain of
  * the later positions waits for them.  Errors as for ptycho_loss_grad, and
- * PTYCHO_ERR_ARG when an array is a device pointer; a device-side error
+ * PTYCHO_ERR_ARG when an array is a device pointer.  A device-side error
  * (a bounded wait that gave up, the FP16 range) is returned by this call
- * itself, with its results left undefined, as ptycho_plan_status would.  The paper has no
- * counterpart: it is a packaging of the same kernels. */
+ * itself, as ptycho_plan_status would return it, and the results are then
+ * undefined.  The paper has no counterpart: it is a packaging of the same
+ * kernels. */
 PTYCHO_API int ptycho_loss_grad_host(ptycho_plan plan, const int32_t* pos_yx, const ptycho_c64* probe,
                      const ptycho_c64* obj, const float* meas_I, double* loss_out,
                      ptycho_c64* grad_obj, ptycho_c64* grad_probe, void* stream);
