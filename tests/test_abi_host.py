@@ -63,6 +63,9 @@ def test_version_and_parameter_validation(lib):
     assert lib.ptycho_plan_create(C.byref(h), C.byref(p)) == PTYCHO_ERR_ARG
     assert lib.ptycho_plan_create(None, C.byref(p)) == PTYCHO_ERR_ARG
     assert lib.ptycho_loss_grad(None, None, None, None, None, None, None, None, None) == PTYCHO_ERR_ARG
+    assert lib.ptycho_loss_grad_host(None, None, None, None, None, None, None, None, None) == PTYCHO_ERR_ARG
+    assert b"plan is NULL" in lib.ptycho_last_error()
+    assert lib.ptycho_multi_loss_grad(None, -1, None) == PTYCHO_ERR_ARG
     assert lib.ptycho_plan_destroy(None) == PTYCHO_ERR_ARG
 
 
