@@ -1,11 +1,17 @@
 """Planted mistakes in the oracle must fail its pins.
 
 Each case patches one plausible slip into a copy of the oracle's per-position
-gradient (CPU only) and checks that the finite-difference pin rejects it.
+gradient, multislice model or step (CPU only) and checks that a pin rejects
+it: the finite-difference pin for slips in the adjoint, the dense-matrix
+multislice pin for slips in the order of the forward model (which the
+finite-difference pin cannot see: a wrong forward model with its own exact
+adjoint is still self-consistent), and the brute-force Armijo pin for slips
+in the line search.
 """
 import numpy as np
 import pytest
 
+import test_oracle_pins as pins
 from oracle import ptycho_oracle as orc
 from paper_2205_06327_gb300 import synth
 
@@ -75,3 +81,78 @@ def test_correct_variant_passes():
 ])
 def test_planted_mistake_is_caught(kw):
     assert _fd_mismatch(_variant(**kw)) > 1e-3
+
+
+# ------------------------------------------------- order of the forward model
+
+def _slices_reversed(probe, obj, r, h):
+    """Slip: the slices applied last-to-first."""
+    return _ordered(probe, obj[::-1], r, h, prop_first=False)
+
+
+def _propagate_before_transmit(probe, obj, r, h):
+    """Slip: every slice propagates the incoming wave before its transmission
+    (phi_s = prop(psi_s) O_s), instead of transmitting and then propagating."""
+    return _ordered(probe, obj, r, h, prop_first=True)
+
+
+def _ordered(probe, obj, r, h, prop_first):
+    S, M = obj.shape[0], probe.shape[0]
+    psi, phi = [], []
+    cur = probe.astype(np.complex128)
+    for s in range(S):
+        if prop_first:
+            cur = orc.propagate(cur, h)
+        psi.append(cur)
+        ph = cur * orc.window(obj[s], r, M)
+        phi.append(ph)
+        if not prop_first and s < S - 1:
+            cur = orc.propagate(ph, h)
+        elif prop_first:
+            cur = ph
+    return psi, phi, orc.fft2(phi[-1])
+
+
+def test_correct_order_passes_dense_pin():
+    pins.check_against_dense(*pins._multislice_problem(3, 43))
+
+
+@pytest.mark.parametrize("slip", [_slices_reversed, _propagate_before_transmit])
+def test_planted_order_mistake_is_caught_by_dense_pin(monkeypatch, slip):
+    monkeypatch.setattr(orc, "multislice_waves", slip)
+    with pytest.raises(AssertionError):
+        pins.check_against_dense(*pins._multislice_problem(3, 43))
+
+
+# ------------------------------------------------------------- line search
+
+def _armijo_variant(accept_first_halving=False, drop_alpha=False):
+    def step(probe, obj, pos, I, h, alpha_obj, alpha_probe, line_search=False, c=1e-4, max_halvings=20):
+        F0, gO, gP = orc.loss_grad(probe, obj, pos, I, h)
+        na = 1.0 if drop_alpha else alpha_obj
+        npb = 1.0 if drop_alpha else alpha_probe
+        decrease = na * np.sum(np.abs(gO) ** 2) + npb * np.sum(np.abs(gP) ** 2)
+        t = 1.0
+        for k in range(max_halvings + 1):
+            Pn, On = probe - t * alpha_probe * gP, obj - t * alpha_obj * gO
+            if orc.loss(Pn, On, pos, I, h) <= F0 - c * t * decrease or (accept_first_halving and k == 1):
+                return Pn, On, F0, t
+            t *= 0.5
+        return probe.copy(), obj.copy(), F0, 0.0
+    return step
+
+
+def test_correct_armijo_variant_passes():
+    for case in pins.ARMIJO_CASES:
+        pins.check_armijo(_armijo_variant(), *case)
+
+
+@pytest.mark.parametrize("kw", [dict(accept_first_halving=True), dict(drop_alpha=True)])
+def test_planted_armijo_mistake_is_caught(kw):
+    failed = 0
+    for case in pins.ARMIJO_CASES:
+        try:
+            pins.check_armijo(_armijo_variant(**kw), *case)
+        except AssertionError:
+            failed += 1
+    assert failed >= 1

@@ -9,6 +9,7 @@ file runs in seconds on CPU.
 import numpy as np
 import pytest
 
+import dense_multislice as dm
 from oracle import ptycho_oracle as orc
 from paper_2205_06327_gb300 import synth
 
@@ -190,6 +191,73 @@ def test_single_slice_gradient_by_explicit_jacobian():
     assert np.isclose(L, Ltot, rtol=1e-12)
     assert np.allclose(gO[0].ravel(), go, atol=1e-10)
     assert np.allclose(gP.ravel(), gp, atol=1e-10)
+
+
+def _multislice_problem(S, seed):
+    """Tiny window, strong propagation (phases up to ~4 rad at the band edge),
+    non-unimodular slices that differ from one another."""
+    g = synth.rng(seed)
+    M, H, W = 6, 10, 11
+    probe = _rand_c(g, (M, M))
+    obj = (1 + 0.3 * g.uniform(-1, 1, (S, H, W))) * np.exp(1j * g.uniform(-1.2, 1.2, (S, H, W)))
+    pos = np.array([[0, 0], [4, 1], [2, 5], [3, 3]], np.int32)
+    I = g.uniform(0.1, 4.0, (len(pos), M, M))
+    geo = (0.0251, 2.0, 0.1)
+    return probe, obj, pos, I, orc.fresnel_propagator(M, *geo), dm.fresnel_diag(M, *geo)
+
+
+def check_against_dense(probe, obj, pos, I, h, hd):
+    """The oracle's far fields, loss and gradients against the dense-matrix
+    product of Sec. II-B's multislice model (tests/dense_multislice.py)."""
+    far = orc.forward(probe, obj, pos, h)
+    for i, r in enumerate(pos):
+        _, Psi, _, _ = dm.position(probe, obj, r, I[i], hd)
+        assert np.allclose(far[i].ravel(), Psi, rtol=0, atol=1e-12 * np.abs(Psi).max())
+    L, gO, gP = orc.loss_grad(probe, obj, pos, I, h)
+    Ld, gOd, gPd = dm.loss_grad(probe, obj, pos, I, hd)
+    assert np.isclose(L, Ld, rtol=1e-12)
+    assert np.allclose(gO, gOd, rtol=0, atol=1e-11 * np.abs(gOd).max())
+    assert np.allclose(gP, gPd, rtol=0, atol=1e-11 * np.abs(gPd).max())
+
+
+@pytest.mark.parametrize("S", [2, 3])
+def test_multislice_composition_by_dense_matrices(S):
+    """S >= 2 (Sec. II-B: the output of one slice is the input of the next):
+    Psi = D T_{S-1} D^H diag(h) D ... T_1 D^H diag(h) D T_0 P with explicit
+    matrices fixes the slice order, that each transmission precedes the
+    propagation, and the adjoint of the whole chain (g = J^H g_Psi)."""
+    check_against_dense(*_multislice_problem(S, 40 + S))
+
+
+ARMIJO_CASES = [(1.0, 1e-3, "halved"), (1e-5, 1e-6, "full")]
+
+
+def check_armijo(step_fn, aO, aP, expect):
+    """Brute force over t = 1, 1/2, 1/4, ...: step_fn must return the first t
+    with F(x - t a g) <= F(x) - 1e-4 t (a_O |g_O|^2 + a_P |g_P|^2).  The long
+    steps need several halvings (a slip that accepts the first halving, or
+    halves once too often, fails); with the short steps t = 1 passes while the
+    same test with the step sizes left out of the decrease term accepts no t."""
+    probe, obj, pos, I, h = _small_problem()
+    L0, gO, gP = orc.loss_grad(probe, obj, pos, I, h)
+    nO, nP = np.sum(np.abs(gO) ** 2), np.sum(np.abs(gP) ** 2)
+    ts = [0.5 ** k for k in range(21)]
+    F = {t: orc.loss(probe - t * aP * gP, obj - t * aO * gO, pos, I, h) for t in ts}
+    first = next(t for t in ts if F[t] <= L0 - 1e-4 * t * (aO * nO + aP * nP))
+    if expect == "halved":
+        assert first <= 0.125
+    else:
+        assert first == 1.0
+        assert not any(F[t] <= L0 - 1e-4 * t * (nO + nP) for t in ts)
+    Pn, On, F0, t = step_fn(probe, obj, pos, I, h, aO, aP, line_search=True)
+    assert F0 == L0 and t == first
+    assert np.allclose(On, obj - t * aO * gO, rtol=0, atol=1e-14)
+    assert np.allclose(Pn, probe - t * aP * gP, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("aO, aP, expect", ARMIJO_CASES)
+def test_armijo_accepts_the_first_passing_halving(aO, aP, expect):
+    check_armijo(orc.step, aO, aP, expect)
 
 
 def test_orthogonality_identities():
