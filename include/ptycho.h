@@ -270,10 +270,18 @@ PTYCHO_API int ptycho_plan_timing(ptycho_plan plan, ptycho_timing* out, int32_t 
  * nothing -- no plan, no cudaMalloc/cudaFree, no allocating library call.
  * The paper has no counterpart: this is the same kernels, differently fed.
  *
+ * Limits: M = 64 or 128 only (other windows: PTYCHO_ERR_UNSUPPORTED),
+ * PTYCHO_FP32 only, and every wave is kept (no recompute mode:
+ * params->ckpt_every is ignored).
+ *
  * Scratch: one static device array of 64 MiB, held by every GPU that loads
- * the library until the process exits.  Positions run in chunks that fit in
- * it; a problem whose single position needs more than it holds (about
- * (2S) * M * M * 8 bytes plus 4 MiB) returns PTYCHO_ERR_UNSUPPORTED.
+ * the library until the process exits.  A fixed part (the twiddle and
+ * propagator tables, 4 * M * M * 8 bytes of probe-gradient partials and a few
+ * words; about 0.5 MiB at M = 128) comes first; positions then run in chunks
+ * that fit in the rest, each position needing
+ *     (2S - 1) * M * M * 8 + M * M * 8 + 8 bytes
+ * (S = 253 is the deepest chain at M = 128, S = 1021 at M = 64).  A problem whose
+ * single position does not fit returns PTYCHO_ERR_UNSUPPORTED.
  * The first call on a device looks up the array's device address (and sets
  * the kernels' shared-memory limit); make that first call before any stream
  * capture.  Every call shares the array and keeps the previous call's
@@ -281,14 +289,17 @@ PTYCHO_API int ptycho_plan_timing(ptycho_plan plan, ptycho_timing* out, int32_t 
  * overlap on the GPU -- two streams, two host threads, two devices sharing
  * nothing else are fine only if they do not run at the same time on the same
  * device -- race on it.
- *   params     problem description (tile_h/tile_w as for plans; flags and
- *              workspace_bytes are ignored)
- *   pos_yx, probe, obj, meas_I, grad_obj, grad_probe: as ptycho_loss_grad
+ *   params     problem description (tile_h/tile_w as for plans; flags,
+ *              workspace_bytes and ckpt_every are ignored)
+ *   pos_yx, probe, obj, meas_I, grad_obj, grad_probe: as ptycho_loss_grad,
+ *              device pointers, 8-byte aligned (else PTYCHO_ERR_ARG, checked
+ *              before anything is launched)
  *   loss_out   double[1], device or host (required)
  * Positions are checked on the device; the call then synchronises the stream
  * and returns PTYCHO_ERR_POSITION if a window lay outside the object (that
- * window contributes nothing).  Errors are reported by the return code only
- * (ptycho_last_error() is not updated). */
+ * window contributes nothing; the loss and gradients of the others are still
+ * written).  Errors are reported by the return code only (ptycho_last_error()
+ * is not updated). */
 PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, const int32_t* pos_yx,
                                         const ptycho_c64* probe, const ptycho_c64* obj,
                                         const float* meas_I, double* loss_out, ptycho_c64* grad_obj,

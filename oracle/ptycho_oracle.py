@@ -205,7 +205,7 @@ def potential_grad(obj, gO, sigma: float = 1.0):
 
 
 # --------------------------------------------------------------------------
-# Gradient-descent step (Sec. II-B; Alg. 1's update V <- V - alpha dF/dV,
+# Gradient-descent step (Sec. II-B; Algorithm 1's update V <- V - alpha dF/dV,
 # taken here at full batch, i.e. on the position sum of Eq. 2)
 # --------------------------------------------------------------------------
 

@@ -43,6 +43,8 @@ int noalloc_fail(int code, const char* msg) {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
 bool device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -73,6 +75,12 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
   if (!device_ptr(probe) || !device_ptr(obj) || (p.N > 0 && (!device_ptr(meas_I) || !device_ptr(pos_yx))) ||
       (grad_obj && !device_ptr(grad_obj)) || (grad_probe && !device_ptr(grad_probe)))
     return noalloc_fail(PTYCHO_ERR_ARG, "arrays must be device pointers");
+  // The kernels move positions and complex values as 8-byte int2 / float2
+  // and intensities as floats: a misaligned array is an argument error here,
+  // never a misaligned access on the device.
+  if (!aligned8(probe) || !aligned8(obj) || (p.N > 0 && (!aligned8(pos_yx) || !aligned8(meas_I))) ||
+      !aligned8(grad_obj) || !aligned8(grad_probe) || !aligned8(loss_out))
+    return noalloc_fail(PTYCHO_ERR_ARG, "arrays must be 8-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
 

@@ -17,7 +17,7 @@ On one GPU the library sums the gradient with the owner-computes tiled
 accumulation instead; this module runs the decomposition over any
 torch.distributed process group (gloo ranks on CPU in the tests), with
 non-blocking point-to-point messages as in the paper's asynchronous passes.
-:func:`appp_epoch` runs the paper's pipelined schedule (Alg. 2) on top of them:
+:func:`appp_epoch` runs the paper's pipelined schedule (Algorithm 1) on top of them:
 per-location updates of each extended tile, with the accumulated gradients
 reconciled every T locations.
 """
@@ -148,7 +148,7 @@ def exchange(buf: torch.Tensor, grid, me: Tile, group=None) -> None:
 def appp_epoch(buf_tile: torch.Tensor, acc: torch.Tensor, grid, me: Tile, my_pos: np.ndarray, grad_fn,
                alpha: float, T: int, group=None) -> None:
     """One pass over this rank's probe locations of the paper's asynchronous
-    pipelined schedule (Alg. 2), in place on its extended tile ``buf_tile``
+    pipelined schedule (Algorithm 1), in place on its extended tile ``buf_tile``
     and its accumulated-gradient buffer ``acc`` (both [..., ext height, ext
     width]; ``acc`` carries over between passes).  For the i-th location
     (i = 1, 2, ...): its gradient g_i = grad_fn(index, buf_tile) (the tile's
@@ -174,7 +174,7 @@ def appp_epoch(buf_tile: torch.Tensor, acc: torch.Tensor, grid, me: Tile, my_pos
 
 
 def stitch(tiles_and_bufs, shape) -> torch.Tensor:
-    """The final image from the cores of all tiles (halos dropped), as in Alg. 1."""
+    """The final image from the cores of all tiles (halos dropped), as in Algorithm 1."""
     out = torch.zeros(shape, dtype=tiles_and_bufs[0][1].dtype)
     for t, b in tiles_and_bufs:
         out[..., t.core.y0:t.core.y1, t.core.x0:t.core.x1] = _view(b, t.ext, t.core)

@@ -1,11 +1,11 @@
 """Sequential (mini-batch) gradient descent over the probe positions.
 
-Alg. 1 updates the reconstruction after every probe location (its inner loop:
+Algorithm 1 updates the reconstruction after every probe location (its inner loop:
 per-position gradient, then the update), accumulating the gradient over a
 period T for the exchange between GPUs.  On one GPU the data-parallel
 evaluation is the full-batch gradient of Eq. 2; this module gives the
 sequential variant: the positions, in the caller's (raster) order, are taken
-in batches of ``batch`` (1 = Alg. 1's per-position update, N = full batch),
+in batches of ``batch`` (1 = Algorithm 1's per-position update, N = full batch),
 and after each batch O and P are updated with that batch's gradient.  Every
 batch is one ``ptycho_step`` call on the library's kernels.
 """

@@ -1,6 +1,6 @@
 """Seeded synthetic inputs shaped like the paper's workloads.
 
-The paper evaluates on simulated PbTiO3 datasets (Sec. V-A, Table I) that are
+The paper evaluates on simulated PbTiO3 datasets (Sec. VI-A, Table I) that are
 not distributed with it.  This module builds stand-ins with the same
 structure: a raster scan of probe positions with heavy overlap (Fig. 3), a
 defocused probe from a circular aperture, and a stack of complex

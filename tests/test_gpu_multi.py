@@ -129,7 +129,7 @@ def test_autotuner_picks_and_caches_a_tile(dev, tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("batch", [1, 3, 7])
 def test_sequential_gd_matches_oracle_steps(dev, batch):
-    """Alg. 1's sequential update (batch = 1) and mini-batches: one epoch of
+    """Algorithm 1's sequential update (batch = 1) and mini-batches: one epoch of
     updates after every batch, against the same sequence of FP64 oracle steps."""
     from paper_2205_06327_gb300 import api
     from paper_2205_06327_gb300.sgd import SequentialGD
@@ -156,9 +156,9 @@ def test_sequential_gd_matches_oracle_steps(dev, batch):
 
 
 def test_sequential_gd_convergence_by_batch(dev):
-    """Loss against epochs for Alg. 1's per-position updates, mini-batches and
+    """Loss against epochs for Algorithm 1's per-position updates, mini-batches and
     the full batch at the same step size (the paper's question of how often to
-    update, Sec. V): every schedule lowers the cost every epoch, and at this
+    update, Sec. VI-F, Fig. 9): every schedule lowers the cost every epoch, and at this
     small step the schedules agree to first order (within 1 %)."""
     from paper_2205_06327_gb300 import api
     from paper_2205_06327_gb300.sgd import SequentialGD

@@ -90,7 +90,7 @@ def test_stitching_the_cores_recovers_the_image():
     assert np.array_equal(st.numpy(), gO)
 
 
-# ------------------------------------------------ Alg. 2: pipelined schedule with period T
+# ------------------------------------------------ Algorithm 1: pipelined schedule with period T
 
 ALPHA = 2e-3
 
@@ -164,7 +164,7 @@ def _appp_reference(R, C, T, epochs):
 
 @pytest.mark.parametrize("R,C,T,epochs", [(2, 2, 3, 2), (2, 2, 1000, 1), (1, 3, 5, 1)])
 def test_appp_schedule_matches_the_reconciled_reference(R, C, T, epochs):
-    """Alg. 2 on gloo ranks: per-location updates of each extended tile, the
+    """Algorithm 1 on gloo ranks: per-location updates of each extended tile, the
     buffers reconciled by the passes every T locations (T = 1000: once, after
     the largest rank's last location), then the second update."""
     world = R * C
