@@ -38,9 +38,7 @@ if ROOT not in sys.path:
 
 METRIC = "probe-positions/s for loss+object/probe gradient; % of HBM/tensor roofline"
 UNIT = "positions/s"
-FP32_LANES_PER_SM = 128
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM (4 partitions x 32)
 
 
 # --------------------------------------------------------------------------
@@ -107,11 +105,17 @@ def hbm_bytes_per_evaluation(wl) -> float:
 _ORC_STATE = {}
 
 
+def _as_c64(a):
+    """The complex64 values the GPU receives, widened again for the oracle."""
+    return np.asarray(a).astype(np.complex64).astype(np.complex128)
+
+
 def _oracle_init(config_id: int):
     from oracle import ptycho_oracle as orc
     wl = workload_for(config_id)
     _ORC_STATE["wl"] = wl
-    _ORC_STATE["obj"] = start_object(wl)
+    _ORC_STATE["probe"] = _as_c64(wl.probe)
+    _ORC_STATE["obj"] = _as_c64(start_object(wl))
     _ORC_STATE["h"] = orc.fresnel_propagator(wl.M, wl.lambda_A, wl.dz_A, wl.pixel_A)
 
 
@@ -119,7 +123,8 @@ def _oracle_task(args):
     from oracle import ptycho_oracle as orc
     idx, I = args
     wl = _ORC_STATE["wl"]
-    L, gO, gP = orc.loss_grad(wl.probe, _ORC_STATE["obj"], wl.pos[idx], I.astype(np.float64), _ORC_STATE["h"])
+    L, gO, gP = orc.loss_grad(_ORC_STATE["probe"], _ORC_STATE["obj"], wl.pos[idx], I.astype(np.float64),
+                              _ORC_STATE["h"])
     # return only the bounding box of the windows touched
     y0, x0 = wl.pos[idx].min(0)
     y1, x1 = wl.pos[idx].max(0) + wl.M
@@ -133,8 +138,9 @@ class OraclePool:
         self.pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(config_id,))
         self.pool.map(abs, range(cores))  # wait for the workers
 
-    def evaluate(self, wl, idx: np.ndarray, I: np.ndarray) -> float:
-        """One oracle loss+gradient over positions idx (I rows for them); returns wall seconds."""
+    def loss_grad(self, wl, idx: np.ndarray, I: np.ndarray):
+        """One oracle loss+gradient over positions idx (I rows for them):
+        (F, dF/dO, dF/dP, wall seconds)."""
         parts = np.array_split(np.asarray(idx), min(self.cores, len(idx)))
         t0 = time.perf_counter()
         res = self.pool.map(_oracle_task, [(p, I[p]) for p in parts if len(p)])
@@ -145,7 +151,11 @@ class OraclePool:
             L += l
             gO[:, y0:y0 + g.shape[1], x0:x0 + g.shape[2]] += g
             gP += p
-        return time.perf_counter() - t0
+        return L, gO, gP, time.perf_counter() - t0
+
+    def evaluate(self, wl, idx: np.ndarray, I: np.ndarray) -> float:
+        """One oracle loss+gradient over positions idx; returns wall seconds."""
+        return self.loss_grad(wl, idx, I)[3]
 
     def close(self):
         self.pool.close()
@@ -335,6 +345,179 @@ def run_reference(args, world, rank):
     return 0
 
 
+def fp32_peak(device, sm_mhz) -> tuple[float, str]:
+    """FP32 ALU peak (TFLOP/s) of the device that ran: its SM count times 128
+    FMA lanes times 2 flops at the median SM clock sampled in the timed region
+    (the nominal maximum clock if no sample was taken)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz, how = sm_mhz, "median SM clock sampled in the timed region"
+    if not mhz:
+        mhz, how = 2070.0, "nominal maximum clock (no clock samples)"
+    return (sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            f"derived: {sms} SMs (device property) x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {mhz:.0f} MHz "
+            f"({how})")
+
+
+def measure_workload(wl, config_id, args, device, world, rank, local, ckpt_every, steps, warmup, clocks_path):
+    """Time `steps` evaluations of workload wl (after `warmup`) through
+    ptycho_loss_grad with inputs resident in HBM.  Returns the measurement and
+    the device tensors (for the end-to-end and parity legs)."""
+    import torch
+
+    from paper_2205_06327_gb300 import api
+
+    obj0 = start_object(wl)
+    geom = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    tile = (0, 0)
+    plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=ckpt_every,
+                    precision=args.precision)
+    pos = torch.from_numpy(wl.pos).to(device)
+    probe = torch.from_numpy(wl.probe.astype(np.complex64)).to(device)
+    obj_true = torch.from_numpy(wl.obj.astype(np.complex64)).to(device)
+    obj = torch.from_numpy(obj0.astype(np.complex64)).to(device)
+    # measurements: forward model at the truth (GPU), Poisson counts (seeded)
+    _, I = plan.forward(pos, probe, obj_true, want_psi=False, want_intensity=True)
+    del obj_true
+    if wl.counts is not None:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(1000 + config_id)
+        I = torch.poisson(I, generator=gen)
+    if config_id == 3:
+        # The gradient is accumulated per tile; the tile shape only changes the
+        # speed (results are bit-identical), so the 8 x 8 tessellation of the
+        # workload competes with smaller tiles and the fastest is kept.
+        from paper_2205_06327_gb300 import autotune
+        tess = ((wl.H + 7) // 8, (wl.W + 7) // 8)
+        tile = autotune.tune_tile(geom, pos, probe, obj, I, device, precision=args.precision,
+                                  candidates=(tess, (32, 32), (16, 64), (32, 64), (64, 32)), reps=1,
+                                  use_cache=False, ckpt_every=ckpt_every)
+        plan.close()
+        plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=ckpt_every,
+                        precision=args.precision)
+    gO = torch.empty((wl.S, wl.H, wl.W), dtype=torch.complex64, device=device)
+    gP = torch.empty((wl.M, wl.M), dtype=torch.complex64, device=device)
+    loss = torch.empty((), dtype=torch.float64, device=device)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+    lib, h, sh = plan.lib, plan._h, stream.cuda_stream
+
+    def step():
+        rc = lib.ptycho_loss_grad(h, pos.data_ptr(), probe.data_ptr(), obj.data_ptr(), I.data_ptr(),
+                                  loss.data_ptr(), gO.data_ptr(), gP.data_ptr(), sh)
+        if rc:
+            from paper_2205_06327_gb300._lib import check
+            check(rc)
+
+    for _ in range(warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(device)
+    plan.timing(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    clocks = ClockSampler(local, clocks_path)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    wall0 = time.perf_counter()
+    with clocks:
+        for k in range(steps):
+            flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(device)
+    wall = time.perf_counter() - wall0
+    barrier(world, device)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tm = plan.timing(reset=True)
+    plan.status()
+    del flush
+    t_step = float(np.mean(step_ms)) / 1e3
+    t_max = reduce_max(t_step, world, device)
+    csum = clocks.summary()
+
+    # roofline of the dominant kernel (slice chain): FP32 ALU bound, or the
+    # tensor pipe for the split-precision transforms.  Per launch: the
+    # kernel's events on the launching stream cover all chain launches.
+    chain_ms = tm["chain_ms"] / max(tm["chain_launches"], 1)
+    chain_pos = tm["chain_positions"] / max(tm["chain_launches"], 1)
+    # recompute mode: K launches share one evaluation's chain work
+    chain_work = tm["chain_positions"] / max(wl.N * steps, 1)
+    if args.precision != "fp32":
+        chain_flops = tensor_flops_per_position(wl.M, wl.S) * chain_pos / chain_work
+        pk_t = peaks_tensor()
+        peak_tflops = pk_t["bf16_tflops"]
+        bound, peak_src = "tensor", pk_t["src"]
+    else:
+        chain_flops = chain_flops_per_position(wl.M, wl.S) * chain_pos / chain_work
+        peak_tflops, peak_src = fp32_peak(device, csum["sm_mhz"])
+        bound = "alu"
+    achieved = chain_flops / (chain_ms / 1e3) / 1e12
+    tpp = measured_traffic_per_position(args.precision, wl.M, wl.S) if not ckpt_every else None
+    traffic = tpp * chain_pos if tpp is not None else None
+    pk = peaks()
+    # accumulation, per launch: the workspace arrays it reads (conj(psi) and
+    # g_phi per slice, or the finished patches in recompute mode) for the
+    # launch's positions and slices, and the object gradient (written by a
+    # step's first launch of each slice, read and rewritten by the later ones)
+    n_acc = max(tm["accum_launches"], 1)
+    accum_ms = tm["accum_ms"] / n_acc
+    per_step = n_acc / steps
+    if ckpt_every:  # one launch per (chunk, segment): the segment's slices, the chunk's positions
+        n_seg = -(-wl.S // ckpt_every)
+        n_chunks = per_step / n_seg
+        sl, acc_pos, arrays = wl.S / n_seg, wl.N / n_chunks, 1.0
+        grad_bytes = sl * wl.H * wl.W * 8 * (1.0 + 2.0 * (n_chunks - 1)) / n_chunks
+    else:           # one or two launches per chunk (full waves, tail): every slice
+        sl, acc_pos, arrays = wl.S, wl.N / per_step, 2.0
+        grad_bytes = wl.S * wl.H * wl.W * 8 * (1.0 + 2.0 * (per_step - 1)) / per_step
+    accum_bytes = arrays * acc_pos * sl * wl.M * wl.M * 8 + grad_bytes
+    launches_per_step = tm["launches"] / steps
+    meas = {
+        "value": world * wl.N / t_max, "t_max": t_max, "step_ms": step_ms, "wall": wall, "tile": tile,
+        "csum": csum, "plan_chunk": plan.chunk, "workspace_bytes": plan.workspace_bytes,
+        "launches_per_step": launches_per_step, "geom": geom,
+        "roofline": {"bound": bound, "kernel": "k_chain (slice chain, gradient mode)"
+                     if args.precision == "fp32" else "k_chain_tc (split DFT products, gradient mode)",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "peak_src": peak_src,
+                     "kernel_ms": chain_ms, "kernel_share": tm["chain_ms"] / max(sum(step_ms), 1e-9)},
+        "hbm_kernels": {"accum_obj_grad": {"ms": accum_ms, "bytes": accum_bytes,
+                                           "gbs": accum_bytes / (accum_ms / 1e3) / 1e9 if accum_ms else None,
+                                           "frac": (accum_bytes / (accum_ms / 1e3) / 1e9) / pk["hbm_gbs"]
+                                           if accum_ms else None, "peak_src": pk["src"]}},
+        "path_bound_ms": max(flops_per_position(wl.M, wl.S) * wl.N / (peak_tflops * 1e12),
+                             hbm_bytes_per_evaluation(wl) / (pk["hbm_gbs"] * 1e9)) * 1e3,
+        "tensors": (pos, probe, obj, I, gO, gP),
+    }
+    plan.close()
+    return meas
+
+
+def parity_sample(wl, args, device, tile, ckpt_every, tensors, pool, k=48):
+    """Relative errors of the timed path against the FP64 oracle on k positions
+    spread over the scan (outside the timed region): the same kernels, launch
+    configuration and inputs, restricted to those positions."""
+    import torch
+
+    from paper_2205_06327_gb300 import api
+    pos, probe, obj, I = tensors[:4]
+    idx = cpu_sample_indices(wl, k)
+    sel = torch.from_numpy(idx).to(device)
+    g = api.Geometry(wl.M, wl.S, wl.H, wl.W, len(idx), wl.lambda_A, wl.dz_A, wl.pixel_A)
+    plan = api.Plan(g, device, async_check=True, tile=tile, ckpt_every=ckpt_every, precision=args.precision)
+    L, gO, gP = plan.loss_grad(pos[sel].contiguous(), probe, obj, I[sel].contiguous())
+    torch.cuda.synchronize(device)
+    plan.close()
+    Lr, gOr, gPr, _ = pool.loss_grad(wl, idx, I.cpu().numpy())
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"positions": int(len(idx)), "loss": abs(float(L) - Lr) / abs(Lr),
+            "grad_obj": rel(gO.cpu().numpy(), gOr), "grad_probe": rel(gP.cpu().numpy(), gPr),
+            "reference": "FP64 oracle on the complex64 inputs, same positions",
+            "bar": "rel-L2 1e-5 (FP32) / 2e-4 (split precisions)"}
+
+
 def run_gpu(args, world, rank, local, pool):
     import torch
 
@@ -351,104 +534,12 @@ def run_gpu(args, world, rank, local, pool):
         wl.pos = wl.pos[: args.positions]
     if args.order == "shuffled":
         wl.pos = wl.pos[np.random.default_rng(12345).permutation(len(wl.pos))]
-    obj0 = start_object(wl)
-    geom = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
-    tile = (0, 0)
     if args.ckpt_every is None:  # the PbTiO3-shaped workload recomputes waves in the adjoint:
         args.ckpt_every = 5 if args.config == 3 else 0  # ceil(sqrt(30)) = 6 checkpoints, interval 5
-    plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=args.ckpt_every,
-                    precision=args.precision)
-    pos = torch.from_numpy(wl.pos).to(device)
-    probe = torch.from_numpy(wl.probe.astype(np.complex64)).to(device)
-    obj_true = torch.from_numpy(wl.obj.astype(np.complex64)).to(device)
-    obj = torch.from_numpy(obj0.astype(np.complex64)).to(device)
-    # measurements: forward model at the truth (GPU), Poisson counts (seeded)
-    _, I = plan.forward(pos, probe, obj_true, want_psi=False, want_intensity=True)
-    del obj_true
-    if wl.counts is not None:
-        gen = torch.Generator(device=device)
-        gen.manual_seed(1000 + args.config)
-        I = torch.poisson(I, generator=gen)
-    if args.config == 3:
-        # The gradient is accumulated per tile; the tile shape only changes the
-        # speed (results are bit-identical), so the 8 x 8 tessellation of the
-        # workload competes with smaller tiles and the fastest is kept.
-        from paper_2205_06327_gb300 import autotune
-        tess = ((wl.H + 7) // 8, (wl.W + 7) // 8)
-        tile = autotune.tune_tile(geom, pos, probe, obj, I, device, precision=args.precision,
-                                  candidates=(tess, (32, 32), (16, 64), (32, 64), (64, 32)), reps=1,
-                                  use_cache=False, ckpt_every=args.ckpt_every)
-        plan.close()
-        plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=args.ckpt_every,
-                        precision=args.precision)
-    gO = torch.empty((wl.S, wl.H, wl.W), dtype=torch.complex64, device=device)
-    gP = torch.empty((wl.M, wl.M), dtype=torch.complex64, device=device)
-    loss = torch.empty((), dtype=torch.float64, device=device)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
-    stream = torch.cuda.current_stream(device)
-    lib, h, sh = plan.lib, plan._h, stream.cuda_stream
-
-    def step():
-        rc = lib.ptycho_loss_grad(h, pos.data_ptr(), probe.data_ptr(), obj.data_ptr(), I.data_ptr(),
-                                  loss.data_ptr(), gO.data_ptr(), gP.data_ptr(), sh)
-        if rc:
-            from paper_2205_06327_gb300._lib import check
-            check(rc)
-
-    for _ in range(args.warmup):
-        flush.fill_(1)
-        step()
-    torch.cuda.synchronize(device)
-    plan.timing(reset=True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local, f"{args.clocks_csv}.r{rank}.csv" if args.clocks_csv else None)
-    barrier(world, device)
-    torch.cuda.synchronize(device)
-    wall0 = time.perf_counter()
-    with clocks:
-        for k in range(args.steps):
-            flush.fill_(k & 0xff)
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize(device)
-    wall = time.perf_counter() - wall0
-    barrier(world, device)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tm = plan.timing(reset=True)
-    plan.status()
-    t_step = float(np.mean(step_ms)) / 1e3
-    t_max = reduce_max(t_step, world, device)
-    value = world * wl.N / t_max
-
-    # roofline of the dominant kernel (slice chain): FP32 ALU bound, or the
-    # tensor pipe for the BF16-split transforms
-    chain_ms = tm["chain_ms"] / max(tm["chain_launches"], 1)
-    chain_pos = tm["chain_positions"] / max(tm["chain_launches"], 1)
-    if args.precision != "fp32":
-        chain_flops = tensor_flops_per_position(wl.M, wl.S) * chain_pos
-        pk_t = peaks_tensor()
-        peak_tflops = pk_t["bf16_tflops"]
-        bound, peak_src = "tensor", pk_t["src"]
-    else:
-        chain_flops = chain_flops_per_position(wl.M, wl.S) * chain_pos
-        peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        bound, peak_src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    achieved = chain_flops / (chain_ms / 1e3) / 1e12
-    tpp = measured_traffic_per_position(args.precision, wl.M, wl.S)
-    traffic = tpp * chain_pos if tpp is not None else None
-    pk = peaks()
-    # accumulation, per launch: the workspace arrays it reads (conj(psi) and
-    # g_phi per slice, or the finished patches in recompute mode) for the
-    # launch's positions, and the object gradient (written by a step's first
-    # launch, read and rewritten by the later ones)
-    n_acc = max(tm["accum_launches"], 1)
-    accum_ms = tm["accum_ms"] / n_acc
-    acc_pos = wl.N * args.steps / n_acc
-    per_step = n_acc / args.steps
-    obj_bytes = wl.S * wl.H * wl.W * 8 * (1.0 + 2.0 * (per_step - 1)) / per_step
-    accum_bytes = (1.0 if args.ckpt_every else 2.0) * acc_pos * wl.S * wl.M * wl.M * 8 + obj_bytes
-    launches_per_step = tm["launches"] / args.steps
+    m = measure_workload(wl, args.config, args, device, world, rank, local, args.ckpt_every, args.steps,
+                         args.warmup, f"{args.clocks_csv}.r{rank}.csv" if args.clocks_csv else None)
+    pos, probe, obj, I, gO, gP = m["tensors"]
+    geom, tile = m["geom"], m["tile"]
 
     # end to end through the public API: pinned host inputs, host results
     e2e = None
@@ -458,6 +549,7 @@ def run_gpu(args, world, rank, local, pool):
         d2h = 8 + gO.numel() * 8 + gP.numel() * 8
         eplan = api.Plan(geom, device, async_check=True, tile=tile, ckpt_every=args.ckpt_every,
                          precision=args.precision)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
         # warm-up as in the timed loop: the previous results stay alive while
         # the next call runs, so the pinned result buffers are all allocated
         for _ in range(3):
@@ -472,12 +564,13 @@ def run_gpu(args, world, rank, local, pool):
             _ = float(L)
             ts.append(time.perf_counter() - t0)
         eplan.close()
+        del flush
         print("e2e ms per evaluation: " + " ".join(f"{1e3 * t:.3f}" for t in ts), file=sys.stderr)
         te = reduce_max(float(np.mean(ts)), world, device)
         e2e = {"value": world * wl.N / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    cpu = None
+    cpu, parity = None, None
     if pool is not None and rank == 0:
         idx = cpu_sample_indices(wl, args.cpu_sample)
         I_host = I.cpu().numpy()
@@ -486,35 +579,45 @@ def run_gpu(args, world, rank, local, pool):
         cpu = {"value": len(idx) / t_cpu, "unit": UNIT, "cores": pool.cores, "cpu": cpu_model(), "kind": "oracle",
                "sample": f"{len(idx)} of {wl.N} positions, one loss + object/probe gradient evaluation "
                          f"(FP64 NumPy, process pool)"}
+        if not args.positions and args.order == "raster":
+            parity = parity_sample(wl, args, device, tile, args.ckpt_every, m["tensors"], pool)
+    del pos, probe, obj, I, gO, gP, m["tensors"]
 
-    csum = clocks.summary()
+    # the workload closest to the paper (16632 positions, Table I's count),
+    # timed after the headline measurement
+    paper_shaped = None
+    if args.config == 2 and not args.no_paper_shaped and not args.positions:
+        w3 = workload_for(3)
+        m3 = measure_workload(w3, 3, args, device, world, rank, local, 5, max(3, args.steps // 4), 3, None)
+        del m3["tensors"]
+        paper_shaped = {"workload": w3.name, "positions": w3.N, "M": w3.M, "S": w3.S, "object": [w3.H, w3.W],
+                        "value": m3["value"], "unit": UNIT, "ms_per_step": m3["t_max"] * 1e3,
+                        "steps": max(3, args.steps // 4), "ckpt_every": 5, "tiles": list(m3["tile"]),
+                        "workspace_bytes": m3["workspace_bytes"], "chunk": m3["plan_chunk"],
+                        "roofline": m3["roofline"], "hbm_kernels": m3["hbm_kernels"],
+                        "gpu_launches_per_step": m3["launches_per_step"],
+                        "clocks": {"sm_mhz": m3["csum"]["sm_mhz"], "reasons": m3["csum"]["reasons"]}}
+
+    csum = m["csum"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["t_max"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": wl.name, "positions": wl.N, "M": wl.M, "S": wl.S, "object": [wl.H, wl.W],
                    "tiles": list(tile) if tile != (0, 0) else [32, 32],
                    "l2": "flushed between timed steps (512 MiB write, outside the step events)",
-                   "replicas": world, "wall_s": wall, "ckpt_every": args.ckpt_every, "order": args.order,
-                   "workspace_bytes": plan.workspace_bytes, "chunk": plan.chunk},
-        "roofline": {"bound": bound, "kernel": "k_chain (slice chain, gradient mode)"
-                     if args.precision == "fp32" else "k_chain_tc (split DFT products, gradient mode)",
-                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": traffic,
-                     "peak_src": peak_src,
-                     "kernel_ms": chain_ms, "kernel_share": tm["chain_ms"] / max(sum(step_ms), 1e-9)},
-        "hbm_kernels": {"accum_obj_grad": {"ms": accum_ms, "bytes": accum_bytes,
-                                           "gbs": accum_bytes / (accum_ms / 1e3) / 1e9 if accum_ms else None,
-                                           "frac": (accum_bytes / (accum_ms / 1e3) / 1e9) / pk["hbm_gbs"]
-                                           if accum_ms else None, "peak_src": pk["src"]}},
-        "path_bound_ms": max(flops_per_position(wl.M, wl.S) * wl.N / (peak_tflops * 1e12),
-                             hbm_bytes_per_evaluation(wl) / (pk["hbm_gbs"] * 1e9)) * 1e3,
-        "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(round(launches_per_step * args.steps)),
-        "gpu_launches_per_step": launches_per_step,
+                   "replicas": world, "wall_s": m["wall"], "ckpt_every": args.ckpt_every, "order": args.order,
+                   "workspace_bytes": m["workspace_bytes"], "chunk": m["plan_chunk"]},
+        "roofline": m["roofline"],
+        "hbm_kernels": m["hbm_kernels"],
+        "path_bound_ms": m["path_bound_ms"],
+        "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
+        "gpu_launches": int(round(m["launches_per_step"] * args.steps)),
+        "gpu_launches_per_step": m["launches_per_step"],
         "clocks": {"sm_mhz": csum["sm_mhz"], "sm_max_mhz": csum["sm_max_mhz"], "reasons": csum["reasons"]},
+        "paper_shaped": paper_shaped,
     }
-    plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -641,6 +744,8 @@ def main(argv=None):
                     help="also keep the raw nvidia-smi clock samples of the timed region (<path>.r<rank>.csv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-paper-shaped", action="store_true",
+                    help="skip the second measurement, of the 16632-position PbTiO3-shaped workload")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -118,17 +118,20 @@ typedef struct {
   int32_t tile_h, tile_w;  /* object-gradient accumulation tile (pixels);
                               0 = 32 x 32.  tile_h * tile_w <= 8192. */
   int32_t ckpt_every; /* 0: keep every slice's wave for the adjoint (fastest).
-                         L >= 1: keep a checkpoint every L slices and recompute
-                         each segment's waves during the adjoint; the workspace
-                         per position drops from (2S-1) to S + ceil(S/L) + L + 1
-                         wave-sized buffers and the gradient accumulation reads
-                         half the bytes, for about (S - ceil(S/L)) / (2S - 1)
-                         more FFT work.  L = 0 is used when L >= S.
-                         PTYCHO_CKPT_AUTO: K = ceil(sqrt(S)) checkpoints,
-                         L = ceil(S / K), which keeps about 2 sqrt(S) waves
-                         per position.  Recompute mode applies to the FP32
-                         path with M = 64 or 128; the other paths keep every
-                         wave. */
+                         L >= 1: per-slice recomputation.  Keep the waves
+                         entering every L-th slice (checkpoints), and during
+                         the adjoint rebuild one segment of L slices at a
+                         time from its checkpoint; each segment's gradient
+                         patches are summed into grad_obj before the next
+                         segment is rebuilt.  With K = ceil(S / L) segments
+                         the workspace per position holds K + L wave-sized
+                         buffers (K - 2 checkpoints, one segment, the parked
+                         adjoint state, the probe gradient) instead of 2S,
+                         for (K - 1)(L - 1) extra propagations.  L = 0 is
+                         used when L >= S.  PTYCHO_CKPT_AUTO: K =
+                         ceil(sqrt(S)), L = ceil(S / K): about 2 sqrt(S)
+                         buffers.  Applies to the FP32 path (every window);
+                         the split precisions keep every wave. */
 } ptycho_params;
 
 #define PTYCHO_CKPT_AUTO (-1)  /* ptycho_params.ckpt_every: ceil(sqrt(S)) checkpoints */
@@ -215,6 +218,23 @@ PTYCHO_API int ptycho_loss_grad_host(ptycho_plan plan, const int32_t* pos_yx, co
 PTYCHO_API int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj,
                 const float* meas_I, double alpha_obj, double alpha_probe,
                 int32_t line_search, double* loss_out, double* t_out, void* stream);
+
+/* Algorithm 1's per-location update with its delayed accumulation, for the
+ * positions of this call (one position per call for Algorithm 1 itself):
+ * the update of ptycho_step without line search, O <- O - alpha_obj dF/dO,
+ * P <- P - alpha_probe dF/dP, and the accumulated-gradient buffer
+ * acc <- acc + dF/dO.  With flush != 0 (the caller's counter of locations
+ * reached a multiple of the period T) it then applies the buffer as the
+ * second update, O <- O - alpha_obj acc, and clears it.  On one GPU the
+ * whole object is one tile, so the passes that would add the neighbouring
+ * tiles' buffers before the second update have nothing to add.
+ *   acc        c64 [S][H][W] device, caller-owned, updated in place
+ *   loss_out   double[1] device or host, or NULL: F (these positions) before the update
+ * The paper updates only V; pass alpha_probe = 0 to keep the probe fixed. */
+PTYCHO_API int ptycho_step_accumulate(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe,
+                                      ptycho_c64* obj, const float* meas_I, double alpha_obj,
+                                      double alpha_probe, ptycho_c64* acc, int32_t flush, double* loss_out,
+                                      void* stream);
 
 /* Several independent reconstructions in one call (the batched workload:
  * problems of different windows, slice counts and sizes).  Each problem has

@@ -42,7 +42,7 @@ EXPORTED = [
     "ptycho_forward", "ptycho_loss_grad", "ptycho_loss_grad_host", "ptycho_step", "ptycho_plan_timing",
     "ptycho_loss_grad_noalloc",
     "ptycho_potential_to_transmission", "ptycho_potential_grad", "ptycho_last_error", "ptycho_version",
-    "ptycho_multi_loss_grad", "ptycho_multi_step",
+    "ptycho_multi_loss_grad", "ptycho_multi_step", "ptycho_step_accumulate",
 ]
 
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "ptycho_loss_grad": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_loss_grad_host": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_step": ([vp, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp], C.c_int),
+        "ptycho_step_accumulate": ([vp, vp, vp, vp, vp, dbl, dbl, vp, i32, vp, vp], C.c_int),
         "ptycho_plan_timing": ([vp, C.POINTER(PtychoTiming), i32], C.c_int),
         "ptycho_loss_grad_noalloc": ([C.POINTER(PtychoParams), vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "ptycho_potential_to_transmission": ([vp, vp, C.c_int64, dbl, vp], C.c_int),

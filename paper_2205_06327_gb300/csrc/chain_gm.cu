@@ -257,6 +257,8 @@ struct GmLineArgs {
   int pre;    // forward transmission on load: [store psi_s], times O_s[window]
   int post;   // adjoint transmission on store: store g_phi_s, times conj(O_s[window])
   int store;  // with pre: keep psi_s in the workspace
+  int psi_slot;   // workspace slot of psi_s (store)
+  int gphi_slot;  // workspace slot of g_phi_s (post)
 };
 
 // Where a stage takes its inputs and puts its outputs: the block's shared
@@ -324,7 +326,7 @@ struct GmCtx {
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      if (g.store) __stcs(a.ws_psi + ((size_t)(g.s - 1) * a.ws_n + il) * MM + at(li, i0 + q * di), x[q]);
+      if (g.store) __stcs(a.ws_psi + ((size_t)g.psi_slot * a.ws_n + il) * MM + at(li, i0 + q * di), x[q]);
       x[q] = cmul(x[q], o[q]);
     }
   }
@@ -354,7 +356,7 @@ struct GmCtx {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const size_t e = at(li, i0 + q * di);
-      __stcs(a.ws_gphi + ((size_t)g.s * a.ws_n + il) * MM + e, x[q]);
+      __stcs(a.ws_gphi + ((size_t)g.gphi_slot * a.ws_n + il) * MM + e, x[q]);
       const float2 gv = cmulc(x[q], o[q]);
       if (g.s == 0)
         __stcs(a.ws_gp + (size_t)il * MM + e, gv);
@@ -663,8 +665,9 @@ struct GmLauncher {
   cudaStream_t st;
   int launches = 0;
 
-  cudaError_t line(int op, int cols, int s = 0, int pre = 0, int post = 0, int store = 0) {
-    const GmLineArgs g{op, cols, s, pre, post, store};
+  cudaError_t line(int op, int cols, int s = 0, int pre = 0, int post = 0, int store = 0, int psi_slot = 0,
+                   int gphi_slot = 0) {
+    const GmLineArgs g{op, cols, s, pre, post, store, psi_slot, gphi_slot};
     const unsigned grid = (unsigned)((size_t)a.n_pos * M / gm_lines(M));
     const size_t smem = gm_fft_smem_bytes(M);
     switch (M) {
@@ -686,17 +689,72 @@ struct GmLauncher {
 // inverse far field (column pass, then row pass ending in the adjoint
 // transmission of slice S-1), then per slice a conjugate-propagation column
 // pass and a row pass ending in the adjoint transmission.
+//
+// Recompute mode (ckpt_L = L, K = ceil(S / L) segments) follows the
+// register-resident kernels' schedule with the chunk's waves in wv:
+// MODE_GRAD_RC runs the forward keeping the waves entering segments 1..K-2
+// (ws_psi slots 0..K-3) and the last segment's waves (slots K-2 ..), the
+// residual, the adjoint through the last segment (g_phi in ws_gphi slots
+// s - s0) and parks wv (slot K-2+L); MODE_RC_SEG rebuilds segment a.seg's
+// waves from its checkpoint (or the probe), restores the parked state, runs
+// the adjoint through the segment and parks it again.  The caller sums each
+// segment's (psi, g_phi) pairs into the object gradient in between.
 cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int M, int* n_launches,
                             cudaStream_t st) {
   if (a.n_pos <= 0) return cudaSuccess;
   GmLauncher g{a, wv, M, GmPlan{}, st};
   if (!gm_supported(M, &g.plan)) return cudaErrorInvalidValue;
   cudaError_t e;
-  const bool grad = mode == MODE_GRAD;
+  const size_t MM = (size_t)M * M;
+  const int L = a.ckpt_L > 0 ? a.ckpt_L : 1;
+  const int K = (a.S + L - 1) / L;
+  const int seg_slot = K - 2, park_slot = K - 2 + L;
+  // wv <-> workspace slot (this launch's positions)
+  auto copy = [&](float2* dst, const float2* src) {
+    return cudaMemcpyAsync(dst, src, (size_t)a.n_pos * MM * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+  };
+  auto slot = [&](int k) { return a.ws_psi + (size_t)k * a.ws_n * MM; };
+  // adjoint through slices s_hi .. s_lo, g_phi_s into slot s - gbase
+  auto adjoint = [&](int s_hi, int s_lo, int gbase) -> cudaError_t {
+    for (int s = s_hi; s >= s_lo; --s) {
+      const int op = s == a.S - 1 ? GM_IFFT : GM_PROP_CONJ;
+      cudaError_t r;
+      if ((r = g.line(op, 1)) != cudaSuccess) return r;
+      if ((r = g.line(op, 0, s, 0, 1, 0, 0, s - gbase)) != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  };
+  if (mode == MODE_RC_SEG) {
+    const int j = a.seg, s0 = j * L, s1 = s0 + L;
+    if (j > 0 && (e = copy(wv, slot(j - 1))) != cudaSuccess) return e;
+    for (int s = s0; s < s1 - 1; ++s) {
+      if ((e = g.line(GM_PROP, 0, s, 1, 0, s > 0, seg_slot + (s - s0))) != cudaSuccess) return e;
+      if ((e = g.line(GM_PROP, 1)) != cudaSuccess) return e;
+    }
+    if (s1 - 1 > 0 && (e = copy(slot(seg_slot + L - 1), wv)) != cudaSuccess) return e;
+    if ((e = copy(wv, slot(park_slot))) != cudaSuccess) return e;
+    if ((e = adjoint(s1 - 1, s0, s0)) != cudaSuccess) return e;
+    if (j > 0 && (e = copy(slot(park_slot), wv)) != cudaSuccess) return e;
+    if (n_launches) *n_launches = g.launches;
+    return cudaSuccess;
+  }
+  const bool grad = mode == MODE_GRAD, rc = mode == MODE_GRAD_RC;
+  const int s_last = (K - 1) * L;  // first slice of the last segment (recompute mode)
   for (int s = 0; s < a.S; ++s) {
     const bool last = s == a.S - 1;
     const int op = last ? GM_FFT : GM_PROP;
-    if ((e = g.line(op, 0, s, 1, 0, grad && s > 0)) != cudaSuccess) return e;
+    int store = 0, ps = 0;
+    if (grad && s > 0) {
+      store = 1;
+      ps = s - 1;
+    } else if (rc && s > 0 && s % L == 0 && s / L <= K - 2) {
+      store = 1;
+      ps = s / L - 1;
+    } else if (rc && s >= s_last) {
+      store = 1;
+      ps = seg_slot + (s - s_last);
+    }
+    if ((e = g.line(op, 0, s, 1, 0, store, ps)) != cudaSuccess) return e;
     if ((e = g.line(op, 1)) != cudaSuccess) return e;
   }
   switch (mode) {
@@ -706,12 +764,10 @@ cudaError_t launch_chain_gm(ChainMode mode, const ChainArgs& a, float2* wv, int 
   }
   ++g.launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (grad) {
-    for (int s = a.S - 1; s >= 0; --s) {
-      const int op = s == a.S - 1 ? GM_IFFT : GM_PROP_CONJ;
-      if ((e = g.line(op, 1)) != cudaSuccess) return e;
-      if ((e = g.line(op, 0, s, 0, 1)) != cudaSuccess) return e;
-    }
+  if (grad && (e = adjoint(a.S - 1, 0, 0)) != cudaSuccess) return e;
+  if (rc) {
+    if ((e = adjoint(a.S - 1, s_last, s_last)) != cudaSuccess) return e;
+    if ((e = copy(slot(park_slot), wv)) != cudaSuccess) return e;
   }
   if (n_launches) *n_launches = g.launches;
   return cudaSuccess;

@@ -14,6 +14,19 @@
 // and the gradient w.r.t. every slice's exit wave (streaming stores); the
 // object gradient conj(psi_s) * g_phi_s is formed and summed per object tile
 // by the deterministic owner-computes reduction in reduce_kernels.cu.
+//
+// Recompute mode (checkpoint every L slices, K = ceil(S / L) segments) runs
+// as K launches so that the workspace does not hold a patch per slice: the
+// first (MODE_GRAD_RC) runs the forward model keeping only the checkpoints
+// entering segments 1..K-2 and the waves of the last segment, then the
+// residual and the adjoint through the last segment, writing its finished
+// gradient patches conj(psi_s) g_phi_s over those waves and parking the
+// adjoint state.  Each later launch (MODE_RC_SEG, segment j = K-2 .. 0)
+// rebuilds segment j's waves from its checkpoint (or the probe) with the
+// forward model's exact operations, runs the adjoint through the segment from
+// the parked state and parks the state again (segment 0: the probe gradient).
+// The host accumulates each segment's patches into the object gradient
+// before the next launch overwrites them.
 #include "fft2d.cuh"
 #include "internal.h"
 #include "../../include/ptycho.h"
@@ -84,12 +97,13 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
   const int2 r = a.pos[gi];
   const int yi = r.x, xi = r.y;
   if (yi < 0 || xi < 0 || yi > a.H - M || xi > a.W - M) {
-    // Window outside the object: contribute nothing, flag the call.
-    if (t == 0) {
+    // Window outside the object: contribute nothing, flag the call.  (The
+    // accumulation skips such windows, so no patch needs clearing.)
+    if (t == 0 && MODE != MODE_RC_SEG) {
       *a.status = PTYCHO_ERR_POSITION;
       if (MODE != MODE_FORWARD) a.loss_part[il] = 0.0;
     }
-    if (MODE == MODE_GRAD || MODE == MODE_GRAD_RC)
+    if (MODE == MODE_GRAD || MODE == MODE_GRAD_RC || (MODE == MODE_RC_SEG && a.seg == 0))
       for (int k = t; k < M * M; k += C::T) a.ws_gp[(size_t)il * M * M + k] = make_float2(0.f, 0.f);
     return;
   }
@@ -101,10 +115,55 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
   // (gradient mode always evaluates at obj itself)
   constexpr bool GRAD = MODE == MODE_GRAD || MODE == MODE_GRAD_RC;
   const float2* dirw = (!GRAD && a.obj_dir) ? a.obj_dir + (size_t)yi * a.W + xi : nullptr;
-  const int L = MODE == MODE_GRAD_RC ? a.ckpt_L : 1;
+  const int L = (MODE == MODE_GRAD_RC || MODE == MODE_RC_SEG) ? a.ckpt_L : 1;
   const int K = (a.S + L - 1) / L;  // segments (recompute mode)
+  // Recompute-mode slots of ws_psi (each [ws_n][M][M]): checkpoints entering
+  // segments 1..K-2 at 0..K-3, the L waves (then patches) of the segment being
+  // differentiated from K-2, the parked adjoint state at K-2+L.
+  auto rc_slot = [&](int slot) { return a.ws_psi + ((size_t)slot * a.ws_n + il) * MM; };
+  const int seg_slot = K - 2, park_slot = K - 2 + L;
 
   float2 v[C::V];
+  if constexpr (MODE == MODE_RC_SEG) {
+    // Segment j of the adjoint with recomputation (j <= K-2, so s1 = s0 + L).
+    const int j = a.seg, s0 = j * L, s1 = s0 + L;
+    if (j == 0) {
+      for_p0<C>(t, [&](int e, int py, int px) { v[e] = ldg2(a.probe + py * M + px); });
+    } else {
+      const float2* ck = rc_slot(j - 1);
+      for_p0<C>(t, [&](int e, int py, int px) { v[e] = __ldcs(ck + py * M + px); });
+    }
+    for (int s = s0; s < s1; ++s) {
+      float2* seg = rc_slot(seg_slot + (s - s0));
+      for_p0<C>(t, [&](int e, int py, int px) { seg[py * M + px] = v[e]; });
+      if (s < s1 - 1) {
+        const float2* ow = objw + (size_t)s * HW;
+        for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmul(v[e], ldg2(ow + (size_t)py * a.W + px)); });
+        fft_fwd<C>(v, sm, tw, t);
+        mul_separable<C, false>(v, hs, t);
+        fft_inv<C>(v, sm, tw, t);
+      }
+    }
+    const float2* park = rc_slot(park_slot);  // written by this thread: coherent loads
+    for_p0<C>(t, [&](int e, int py, int px) { v[e] = park[py * M + px]; });
+    for (int s = s1 - 1; s >= s0; --s) {
+      float2* seg = rc_slot(seg_slot + (s - s0));
+      for_p0<C>(t, [&](int e, int py, int px) {
+        const int k = py * M + px;
+        __stcs(seg + k, cconjmul(seg[k], v[e]));  // conj(psi_s) g_phi_s over psi_s
+      });
+      const float2* ow = objw + (size_t)s * HW;
+      for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmulc(v[e], ldg2(ow + (size_t)py * a.W + px)); });
+      if (s > 0) {
+        fft_fwd<C, true>(v, sm, tw, t);
+        mul_separable<C, true>(v, hs, t);
+        fft_inv<C, true>(v, sm, tw, t);
+      }
+    }
+    float2* out = j > 0 ? rc_slot(park_slot) : a.ws_gp + (size_t)il * MM;
+    for_p0<C>(t, [&](int e, int py, int px) { out[py * M + px] = v[e]; });
+    return;
+  }
   // psi_0 = P
   for_p0<C>(t, [&](int e, int py, int px) {
     float2 p = ldg2(a.probe + py * M + px);
@@ -121,9 +180,13 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
       float2* dst = a.ws_psi + ((size_t)(s - 1) * a.ws_n + il) * MM;
       for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
     }
-    if (MODE == MODE_GRAD_RC && s > 0 && s % L == 0) {  // checkpoint entering segment s / L
-      float2* dst = a.ws_psi + ((size_t)(s / L - 1) * a.ws_n + il) * MM;
+    if (MODE == MODE_GRAD_RC && s > 0 && s % L == 0 && s / L <= K - 2) {  // checkpoint entering segment s / L
+      float2* dst = rc_slot(s / L - 1);
       for_p0<C>(t, [&](int e, int py, int px) { __stcs(dst + py * M + px, v[e]); });
+    }
+    if (MODE == MODE_GRAD_RC && s >= (K - 1) * L) {  // the last segment's waves
+      float2* dst = rc_slot(seg_slot + (s - (K - 1) * L));
+      for_p0<C>(t, [&](int e, int py, int px) { dst[py * M + px] = v[e]; });
     }
     // phi_s = psi_s * O_s[window]  (O + step * dir during a line search)
     const float2* ow = objw + (size_t)s * HW;
@@ -198,50 +261,28 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
         }
       }
     } else {
-      // Recompute mode: per segment [s0, s1), park the adjoint state, rebuild
-      // the segment's entering waves from its checkpoint (the forward model's
-      // exact operations, so the same values), then run the adjoint through the
-      // segment writing the finished gradient patches.
+      // Recompute mode, first launch: the adjoint through the last segment
+      // [s0, S), whose waves the forward kept, then park the state for the
+      // launch of segment K-2.
       fft_inv<C, true>(v, sm, tw, t);
-      float2* park = a.ws_psi + ((size_t)(K - 1 + L) * a.ws_n + il) * MM;
-      for (int j = K - 1; j >= 0; --j) {
-        const int s0 = j * L, s1 = min(s0 + L, a.S);
-        for_p0<C>(t, [&](int e, int py, int px) { park[py * M + px] = v[e]; });
-        if (j == 0) {
-          for_p0<C>(t, [&](int e, int py, int px) { v[e] = ldg2(a.probe + py * M + px); });
-        } else {  // written by this thread earlier in this kernel: coherent loads
-          const float2* ck = a.ws_psi + ((size_t)(j - 1) * a.ws_n + il) * MM;
-          for_p0<C>(t, [&](int e, int py, int px) { v[e] = ck[py * M + px]; });
-        }
-        for (int s = s0; s < s1; ++s) {
-          float2* seg = a.ws_psi + ((size_t)(K - 1 + (s - s0)) * a.ws_n + il) * MM;
-          for_p0<C>(t, [&](int e, int py, int px) { seg[py * M + px] = v[e]; });
-          if (s < s1 - 1) {
-            const float2* ow = objw + (size_t)s * HW;
-            for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmul(v[e], ldg2(ow + (size_t)py * a.W + px)); });
-            fft_fwd<C>(v, sm, tw, t);
-            mul_separable<C, false>(v, hs, t);
-            fft_inv<C>(v, sm, tw, t);
-          }
-        }
-        for_p0<C>(t, [&](int e, int py, int px) { v[e] = park[py * M + px]; });
-        for (int s = s1 - 1; s >= s0; --s) {
-          const float2* seg = a.ws_psi + ((size_t)(K - 1 + (s - s0)) * a.ws_n + il) * MM;
-          float2* patch = a.ws_gphi + ((size_t)s * a.ws_n + il) * MM;
-          for_p0<C>(t, [&](int e, int py, int px) {
-            __stcs(patch + py * M + px, cconjmul(seg[py * M + px], v[e]));  // conj(psi_s) g_phi_s
-          });
-          const float2* ow = objw + (size_t)s * HW;
-          for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmulc(v[e], ldg2(ow + (size_t)py * a.W + px)); });
-          if (s > 0) {
-            fft_fwd<C, true>(v, sm, tw, t);
-            mul_separable<C, true>(v, hs, t);
-            fft_inv<C, true>(v, sm, tw, t);
-          }
-        }
+      const int s0 = (K - 1) * L;
+      for (int s = a.S - 1; s >= s0; --s) {
+        float2* seg = rc_slot(seg_slot + (s - s0));
+        for_p0<C>(t, [&](int e, int py, int px) {
+          const int k = py * M + px;
+          __stcs(seg + k, cconjmul(seg[k], v[e]));  // conj(psi_s) g_phi_s over psi_s
+        });
+        const float2* ow = objw + (size_t)s * HW;
+        for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmulc(v[e], ldg2(ow + (size_t)py * a.W + px)); });
+        fft_fwd<C, true>(v, sm, tw, t);  // s >= s0 >= L >= 1
+        mul_separable<C, true>(v, hs, t);
+        fft_inv<C, true>(v, sm, tw, t);
       }
+      float2* park = rc_slot(park_slot);
+      for_p0<C>(t, [&](int e, int py, int px) { park[py * M + px] = v[e]; });
+      return;
     }
-    if constexpr (GRAD) {
+    if constexpr (MODE == MODE_GRAD) {
       float2* gp = a.ws_gp + (size_t)il * MM;
       for_p0<C>(t, [&](int e, int py, int px) { __stcs(gp + py * M + px, v[e]); });
     }
@@ -262,6 +303,7 @@ static cudaError_t prepare_m() {
   if ((e = cudaFuncSetAttribute(k_chain<M, MODE_FORWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_chain<M, MODE_LOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_chain<M, MODE_GRAD_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_chain<M, MODE_RC_SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_chain<M, MODE_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -285,6 +327,7 @@ static cudaError_t launch_m(ChainMode mode, const ChainArgs& a, cudaStream_t st)
     case MODE_FORWARD: k_chain<M, MODE_FORWARD><<<grid, block, smem, st>>>(a); break;
     case MODE_LOSS: k_chain<M, MODE_LOSS><<<grid, block, smem, st>>>(a); break;
     case MODE_GRAD_RC: k_chain<M, MODE_GRAD_RC><<<grid, block, smem, st>>>(a); break;
+    case MODE_RC_SEG: k_chain<M, MODE_RC_SEG><<<grid, block, smem, st>>>(a); break;
     default: k_chain<M, MODE_GRAD><<<grid, block, smem, st>>>(a); break;
   }
   return cudaGetLastError();

@@ -7,11 +7,14 @@
 
 namespace ptycho {
 
-// MODE_GRAD stores every slice's entering wave and exit-wave gradient;
-// MODE_GRAD_RC (recompute) stores checkpoints every ckpt_L slices, recomputes
-// each segment's waves during the adjoint and writes finished gradient
-// patches conj(psi_s) g_phi_s.
-enum ChainMode { MODE_FORWARD = 0, MODE_LOSS = 1, MODE_GRAD = 2, MODE_GRAD_RC = 3 };
+// MODE_GRAD stores every slice's entering wave and exit-wave gradient.
+// Recompute mode (checkpoint every ckpt_L slices, K segments) is K launches:
+// MODE_GRAD_RC runs the forward model keeping the checkpoints and the last
+// segment's waves, the residual, and the adjoint through the last segment;
+// MODE_RC_SEG (segment ChainArgs::seg = K-2 .. 0) rebuilds one segment's
+// waves from its checkpoint and runs the adjoint through it.  Both write the
+// segment's finished gradient patches conj(psi_s) g_phi_s over its waves.
+enum ChainMode { MODE_FORWARD = 0, MODE_LOSS = 1, MODE_GRAD = 2, MODE_GRAD_RC = 3, MODE_RC_SEG = 4 };
 
 // Arguments of the per-position slice-chain kernel.  Positions
 // [pos_begin, pos_begin + n_pos) of the call are processed, one per block.
@@ -30,10 +33,11 @@ struct ChainArgs {
   const float2* hs;       // [M]   one separable factor of the propagator, times 1/M
   int ws_n;               // positions the workspace holds (slice stride of ws_psi / ws_gphi)
   int ckpt_L;             // recompute mode: checkpoint every ckpt_L slices
+  int seg;                // MODE_RC_SEG: the segment differentiated by this launch
   float2* ws_psi;         // GRAD: [S-1][ws_n][M][M] waves entering slices 1..S-1
-                          // GRAD_RC: [K-1 checkpoints | ckpt_L segment | 1 park][ws_n][M][M]
+                          // recompute: [K-2 checkpoints | ckpt_L segment waves, then
+                          // patches | 1 parked adjoint state][ws_n][M][M]
   float2* ws_gphi;        // GRAD: [S][ws_n][M][M] gradient w.r.t. each slice's exit wave
-                          // GRAD_RC: [S][ws_n][M][M] gradient patches conj(psi_s) g_phi_s
   float2* ws_gp;          // [ws_n][M][M]      per-position probe gradient
   double* loss_part;      // [n_pos]
   float2* psi_out;        // [N][M][M] or null (forward mode)
@@ -78,8 +82,12 @@ struct AccumArgs {
   const float2* ws_psi;     // [S-1][ws_n][M][M]
   const float2* ws_gphi;    // [S][ws_n][M][M]
   float2* grad_obj;         // [S][H][W]
-  int accumulate;           // 0: overwrite the whole gradient, 1: add
+  int accumulate;           // 0: overwrite the slices' gradient, 1: add
   int patch_mode;           // 1: ws_gphi holds finished patches (ws_psi unused)
+  int s_begin, n_slices;    // slices [s_begin, s_begin + n_slices) (n_slices 0: all S)
+  int seg_slots;            // 1: slice s's arrays sit at slot s - s_begin of ws_psi /
+                            // ws_gphi (a recompute segment); 0: ws_psi slot s - 1,
+                            // ws_gphi slot s (every wave kept)
 };
 cudaError_t launch_accum_obj_grad(const AccumArgs& a, cudaStream_t st);
 cudaError_t launch_probe_grad(const float2* ws_gp, int n_pos, int M, float2* part, int n_split,

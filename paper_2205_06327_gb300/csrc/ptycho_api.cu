@@ -178,8 +178,8 @@ struct ptycho_plan_s {
   int64_t ws_bytes = 0;
   float2* d_tw = nullptr;     // [M]
   float2* d_hs = nullptr;     // [M]
-  float2* ws_psi = nullptr;   // [chunk][S-1][M][M]
-  float2* ws_gphi = nullptr;  // [chunk][S][M][M]
+  float2* ws_psi = nullptr;   // [S-1][chunk][M][M] (recompute: [K-2+L+1][chunk][M][M])
+  float2* ws_gphi = nullptr;  // [S][chunk][M][M] (recompute: none)
   float2* ws_gp = nullptr;    // [chunk][M][M]
   float2* wv = nullptr;       // generic-window path: [chunk][M][M] waves of the chunk
   float2* gp_part = nullptr;  // [kProbeSplit][M][M]
@@ -430,7 +430,7 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     r.pos_begin = ca.pos_begin + off;
     r.n_pos = n;
     r.ws_psi = pl->ws_psi + (size_t)off * MM;
-    r.ws_gphi = pl->ws_gphi + (size_t)off * MM;
+    r.ws_gphi = pl->ws_gphi ? pl->ws_gphi + (size_t)off * MM : nullptr;
     r.ws_gp = pl->ws_gp + (size_t)off * MM;
     r.loss_part = pl->loss_part + off;
     return r;
@@ -449,9 +449,14 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     pl->tm.chain_positions += ca.n_pos;
     return PTYCHO_OK;
   };
+  // Recompute mode: K segments of L slices; segment j's patches sit in the
+  // L workspace slots from K-2 (see chain_kernels.cu).
+  const bool recompute = want_grad && pl->ckpt_L > 0;
+  const int rcL = pl->ckpt_L, rcK = recompute ? (p.S + rcL - 1) / rcL : 0;
   // Object-gradient accumulation of positions [c0 + off, c0 + off + n) of
-  // the chunk, whose workspace slots start at off.
-  auto accum_for = [&](int c0, int off, int n, int accumulate, cudaStream_t on) -> int {
+  // the chunk, whose workspace slots start at off; in recompute mode, of the
+  // slices of segment j.
+  auto accum_for = [&](int c0, int off, int n, int accumulate, cudaStream_t on, int j = -1) -> int {
     AccumArgs g{};
     g.pos = a.pos;
     g.pos_begin = c0 + off;
@@ -465,10 +470,20 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     g.probe = a.probe;
     g.ws_n = pl->chunk;
     g.ws_psi = pl->ws_psi + (size_t)off * MM;
-    g.ws_gphi = pl->ws_gphi + (size_t)off * MM;
+    g.ws_gphi = pl->ws_gphi ? pl->ws_gphi + (size_t)off * MM : nullptr;
     g.grad_obj = grad_obj;
     g.accumulate = accumulate;
-    g.patch_mode = pl->ckpt_L ? 1 : 0;
+    if (j >= 0) {  // recompute segment j: the segment's slots
+      if (pl->wv) {  // generic path: waves psi_s and exit-wave gradients g_phi_s
+        g.ws_psi = pl->ws_psi + ((size_t)(rcK - 2) * pl->chunk + off) * MM;
+      } else {       // register-resident path: finished patches over the waves
+        g.ws_gphi = pl->ws_psi + ((size_t)(rcK - 2) * pl->chunk + off) * MM;
+        g.patch_mode = 1;
+      }
+      g.seg_slots = 1;
+      g.s_begin = j * rcL;
+      g.n_slices = (j == rcK - 1 ? p.S : g.s_begin + rcL) - g.s_begin;
+    }
     TIMED_ON(on, K_ACCUM, 1, launch_accum_obj_grad(g, on));
     return PTYCHO_OK;
   };
@@ -479,7 +494,8 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     // side stream, on the SMs the tail leaves idle.  The tail's workspace
     // slots follow the full waves', and its accumulation is added second, so
     // the summation order is fixed.
-    const int tail = (grad_obj && !pl->wv && pl->side && pl->wave > 0 && n > pl->wave) ? n % pl->wave : 0;
+    const int tail =
+        (grad_obj && !recompute && !pl->wv && pl->side && pl->wave > 0 && n > pl->wave) ? n % pl->wave : 0;
     const int n1 = n - tail;
     a.pos_begin = c0;
     a.n_pos = n1;
@@ -492,7 +508,28 @@ int run_loss_grad(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, c
     } else if ((rc = launch_chain_for(a)) != PTYCHO_OK) {
       return rc;
     }
-    if (tail) {
+    if (recompute) {
+      // The first launch differentiated the last segment; each later one
+      // rebuilds and differentiates the segment before it, whose patches
+      // overwrite the previous segment's: accumulate each before the next.
+      for (int j = rcK - 1; j >= 0; --j) {
+        if (j < rcK - 1) {
+          ChainArgs sa = a;
+          sa.n_pos = n;
+          sa.seg = j;
+          if (pl->wv) {
+            int gm_launches = 0;
+            TIMED(K_CHAIN, 0, launch_chain_gm(MODE_RC_SEG, sa, pl->wv, p.M, &gm_launches, st));
+            pl->tm.launches += gm_launches;
+            pl->tm.chain_launches += 1;
+          } else {
+            TIMED(K_CHAIN, 1, launch_chain(p.M, MODE_RC_SEG, sa, st));
+          }
+          pl->tm.chain_positions += n;
+        }
+        if (grad_obj && (rc = accum_for(c0, 0, n, ci > 0, st, j)) != PTYCHO_OK) return rc;
+      }
+    } else if (tail) {
       CUDA_TRY(cudaEventRecord(pl->ev_fork, st));
       if ((rc = launch_chain_for(sub(a, n1, tail))) != PTYCHO_OK) return rc;
       CUDA_TRY(cudaStreamWaitEvent(pl->side, pl->ev_fork, 0));
@@ -574,12 +611,18 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
     while (K * K < p.S) ++K;
     ckpt_req = (p.S + K - 1) / K;
   }
-  pl->ckpt_L = (ckpt_req > 0 && ckpt_req < p.S && p.precision == PTYCHO_FP32 && fused_window(M)) ? ckpt_req : 0;
+  pl->ckpt_L = (ckpt_req > 0 && ckpt_req < p.S && p.precision == PTYCHO_FP32) ? ckpt_req : 0;
   const bool gm = !fused_window(M);
+  // Recompute mode keeps K-2 checkpoints, one segment's L waves (then
+  // patches) and the parked adjoint state: K + L - 1 waves whatever S is for
+  // given K and L (about 2 sqrt(S) with the automatic choice), against
+  // 2S - 1 when every wave is kept.  The generic-window path keeps the
+  // segment's L exit-wave gradients beside its waves (and its wave buffer).
   const int K = pl->ckpt_L ? (p.S + pl->ckpt_L - 1) / pl->ckpt_L : 0;
-  const size_t psi_slots = pl->ckpt_L ? (size_t)(K - 1 + pl->ckpt_L + 1) : (size_t)(p.S - 1);
+  const size_t psi_slots = pl->ckpt_L ? (size_t)(K - 2 + pl->ckpt_L + 1) : (size_t)(p.S - 1);
+  const size_t gphi_slots = pl->ckpt_L ? (gm ? (size_t)pl->ckpt_L : 0) : (size_t)p.S;
   const size_t per_pos =
-      (psi_slots + p.S + (gm ? 1 : 0)) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
+      (psi_slots + gphi_slots + (gm ? 1 : 0)) * MM * sizeof(float2) + MM * sizeof(float2) + sizeof(double);
   const int64_t cap = p.workspace_bytes ? p.workspace_bytes : kDefaultWorkspace;
   int64_t chunk = cap / (int64_t)per_pos;
   // generic-window path: keep the chunk's waves (streamed by every FFT pass)
@@ -608,7 +651,7 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   if (!rc) rc = dev_alloc(&pl->d_tw, M, "twiddles");
   if (!rc) rc = dev_alloc(&pl->d_hs, M, "propagator");
   if (!rc) rc = dev_alloc(&pl->ws_psi, (size_t)pl->chunk * psi_slots * MM, "wave workspace");
-  if (!rc) rc = dev_alloc(&pl->ws_gphi, (size_t)pl->chunk * p.S * MM, "adjoint workspace");
+  if (!rc) rc = dev_alloc(&pl->ws_gphi, (size_t)pl->chunk * gphi_slots * MM, "adjoint workspace");
   if (!rc) rc = dev_alloc(&pl->ws_gp, (size_t)pl->chunk * MM, "probe-gradient workspace");
   if (!rc && gm) rc = dev_alloc(&pl->wv, (size_t)pl->chunk * MM, "generic-window wave buffer");
   if (!rc) rc = dev_alloc(&pl->gp_part, (size_t)kProbeSplit * MM, "probe-gradient partials");
@@ -952,6 +995,30 @@ int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptyc
   g_last_error.clear();
   return step_impl(plan, pos_yx, probe, obj, meas_I, alpha_obj, alpha_probe, line_search, loss_out, t_out,
                    static_cast<cudaStream_t>(stream));
+}
+
+int ptycho_step_accumulate(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe, ptycho_c64* obj,
+                           const float* meas_I, double alpha_obj, double alpha_probe, ptycho_c64* acc,
+                           int32_t flush, double* loss_out, void* stream) {
+  g_last_error.clear();
+  if (!plan) return fail(PTYCHO_ERR_ARG, "plan is NULL");
+  int rc;
+  if ((rc = check_array(acc, "acc", true))) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((rc = step_impl(plan, pos_yx, probe, obj, meas_I, alpha_obj, alpha_probe, 0, loss_out, nullptr, st)))
+    return rc;
+  // step_impl left this call's object gradient in the plan's step buffer
+  const ptycho_params& p = plan->p;
+  const size_t nO = (size_t)p.S * p.H * p.W;
+  float2* A = reinterpret_cast<float2*>(acc);
+  float2* O = reinterpret_cast<float2*>(obj);
+  ptycho_plan pl = plan;
+  TIMED_ON(st, K_OTHER, 1, launch_axpy(A, plan->g_obj, A, 1.0, nO, st));  // AccBuf += dF/dO
+  if (flush) {
+    TIMED_ON(st, K_OTHER, 1, launch_axpy(O, A, O, -alpha_obj, nO, st));  // second update
+    CUDA_TRY(cudaMemsetAsync(A, 0, nO * sizeof(float2), st));
+  }
+  return PTYCHO_OK;
 }
 
 int ptycho_multi_loss_grad(const ptycho_problem* problems, int32_t n, void* stream) {

@@ -39,14 +39,16 @@ __global__ void __launch_bounds__(kAccThreads, PTYCHO_ACC_MIN_BLOCKS) k_accum_ob
   __shared__ int lidx[kAccThreads];
   __shared__ int wcount[kAccThreads / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int s = blockIdx.z;
+  const int z = blockIdx.z;  // slice s_begin + z
+  const int s = a.s_begin + z;
   const int M = a.M;
   const int ty0 = blockIdx.y * a.tile_h, tx0 = blockIdx.x * a.tile_w;
   const int th = min(a.tile_h, a.H - ty0), tw = min(a.tile_w, a.W - tx0);
   const int npix = th * tw;
   const size_t MM = (size_t)M * M;
-  const float2* gphi_s = a.ws_gphi + (size_t)s * a.ws_n * MM;
-  const float2* psi_s = s > 0 && !a.patch_mode ? a.ws_psi + (size_t)(s - 1) * a.ws_n * MM : nullptr;
+  const float2* gphi_s = a.ws_gphi + (size_t)(a.seg_slots ? z : s) * a.ws_n * MM;
+  const float2* psi_s =
+      s > 0 && !a.patch_mode ? a.ws_psi + (size_t)(a.seg_slots ? z : s - 1) * a.ws_n * MM : nullptr;
   float2* out = a.grad_obj + (size_t)s * a.H * a.W;
   constexpr int GROUP = kAccPPT * kAccThreads;
 
@@ -260,7 +262,9 @@ __global__ void k_check_positions(const int2* __restrict__ pos, int n, int M, in
 }  // namespace
 
 cudaError_t launch_accum_obj_grad(const AccumArgs& a, cudaStream_t st) {
-  const dim3 grid((a.W + a.tile_w - 1) / a.tile_w, (a.H + a.tile_h - 1) / a.tile_h, a.S);
+  const int ns = a.n_slices > 0 ? a.n_slices : a.S - a.s_begin;
+  if (a.s_begin < 0 || ns <= 0 || a.s_begin + ns > a.S) return cudaErrorInvalidValue;
+  const dim3 grid((a.W + a.tile_w - 1) / a.tile_w, (a.H + a.tile_h - 1) / a.tile_h, ns);
   k_accum_obj_grad<<<grid, kAccThreads, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -65,6 +65,54 @@ def test_graph_replay_matches_eager_and_oracle(dev):
     me.close()
 
 
+# Every window class of the batched workload (64, 96, 128, 192, 256), slices
+# up to 24, and a workspace small enough that the generic-window problems run
+# their positions in several chunks.
+EVERY_WINDOW = [(64, 24, 2, 2, 9), (96, 5, 2, 3, 9), (128, 16, 2, 2, 21), (192, 3, 2, 2, 13),
+                (256, 6, 2, 3, 11), (64, 1, 3, 3, 9), (128, 2, 2, 2, 19)]
+
+
+def test_graph_replay_every_window_class_against_oracle(dev):
+    """Three gradient-descent iterations of seven problems covering every
+    window class, the first eager and two replayed from one captured CUDA
+    graph, against three FP64 oracle steps: the total update of O and P,
+    element by element, at 1e-5 (for 16 slices and more, the FP32 rounding
+    floor measured by the single-precision model on the first gradient)."""
+    from paper_2205_06327_gb300.multi import MultiProblem
+    from tests.helpers import fp32_chain_loss_grad
+    a_o, a_p = 2e-3, 1e-5
+    probs, host = _problems(dev, EVERY_WINDOW)
+    start = [(p.obj.clone(), p.probe.clone()) for p in probs]
+    mp = MultiProblem(probs, dev, workspace_bytes=len(probs) * (14 << 20))
+    assert any(pl.chunk < p.geom.N for pl, p in zip(mp.plans, probs) if p.geom.M in (96, 192, 256))
+    mp.capture(a_o, a_p, warmup=1)
+    mp.run(2)
+    torch.cuda.synchronize()
+    mp.check_status()
+    for p, (O0, P0), (wl, obj, I) in zip(probs, start, host):
+        P, O = c64(wl.probe), c64(obj)
+        h = propagator(wl)
+        bar_o = bar_p = 1e-5
+        if wl.S >= 16:
+            _, gO, gP = orc.loss_grad(P, O, wl.pos, I.astype(np.float64), h)
+            _, fo, fp = fp32_chain_loss_grad(wl.probe, obj, wl.pos, I, h)
+            bar_o, bar_p = max(bar_o, 1.5 * rel_l2(fo, gO)), max(bar_p, 1.5 * rel_l2(fp, gP))
+        for _ in range(3):
+            P, O, _, _ = orc.step(P, O, wl.pos, I.astype(np.float64), h, a_o, a_p)
+        assert rel_l2(p.obj.cpu().numpy(), O) <= 1e-6 and rel_l2(p.probe.cpu().numpy(), P) <= 1e-6
+        # the total update; the iterates are stored in FP32, which bounds how
+        # well an update can be resolved: a few roundings of |O| each step
+        dO_ref, dP_ref = O - c64(obj), P - c64(wl.probe)
+        bar_o = max(bar_o, 4 * 2.0 ** -24 * np.linalg.norm(O) / np.linalg.norm(dO_ref))
+        bar_p = max(bar_p, 4 * 2.0 ** -24 * np.linalg.norm(P) / np.linalg.norm(dP_ref))
+        eo = rel_l2((p.obj - O0).cpu().numpy(), dO_ref)
+        ep = rel_l2((p.probe - P0).cpu().numpy(), dP_ref)
+        print(f"M={wl.M} S={wl.S} N={wl.N}: update of O {eo:.2e} (bar {bar_o:.1e}), of P {ep:.2e} "
+              f"(bar {bar_p:.1e})")
+        assert eo <= bar_o and ep <= bar_p
+    mp.close()
+
+
 def test_multi_loss_grad_matches_single_calls(dev):
     """One multi-problem call (a generic window among the problems) gives the
     single-problem results bit for bit."""
@@ -184,3 +232,100 @@ def test_sequential_gd_convergence_by_batch(dev):
         print(f"batch {batch:3d}: F per epoch " + " ".join(f"{f:.4e}" for f in F))
         assert all(b < a for a, b in zip(F, F[1:]))
         assert np.allclose(F, curves[wl.N], rtol=1e-2)
+
+
+# ------------------------------------- Algorithm 1's delayed accumulation (period T)
+
+@pytest.mark.parametrize("T", [1, 3, 5])
+def test_delayed_accumulation_matches_oracle_sequence(dev, T):
+    """Per-location updates with the accumulated-gradient buffer: after every
+    T-th location the buffer is applied as a second update and cleared, and it
+    carries over into the next epoch.  Two epochs of 7 locations (so the flushes
+    fall at different places in each epoch) against the same sequence of FP64
+    oracle gradients."""
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300.sgd import SequentialGD
+    wl = synth.workload_random(64, 2, 1, 7, 8, seed=91, amp_jitter=0.1)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    obj0 = start_object(wl, "perturbed", 5)
+    g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    a_o, a_p = 4e-3, 1e-5
+    sgd = SequentialGD(g, 1, dev, period=T)
+    P = to_dev(wl.probe, torch.complex64, dev)
+    O = to_dev(obj0, torch.complex64, dev)
+    pos, meas = to_dev(wl.pos, torch.int32, dev), to_dev(I, torch.float32, dev)
+    losses = [sgd.epoch(pos, P, O, meas, a_o, a_p).cpu().numpy() for _ in range(2)]
+    torch.cuda.synchronize()
+    Pr, Or = c64(wl.probe), c64(obj0)
+    acc = np.zeros_like(Or)
+    h = propagator(wl)
+    ref, i = [], 0
+    for _ in range(2):
+        for k in range(wl.N):
+            F0, gO, gP = orc.loss_grad(Pr, Or, wl.pos[k:k + 1], I[k:k + 1].astype(np.float64), h)
+            ref.append(F0)
+            Or = Or - a_o * gO
+            Pr = Pr - a_p * gP
+            acc += gO
+            i += 1
+            if i % T == 0:
+                Or = Or - a_o * acc
+                acc[:] = 0
+    assert np.allclose(np.concatenate(losses), ref, rtol=1e-5)
+    assert rel_l2(O.cpu().numpy(), Or) <= 1e-6 and rel_l2(P.cpu().numpy(), Pr) <= 1e-6
+    assert rel_l2(sgd.acc.cpu().numpy(), acc) <= 1e-5 if np.any(acc) else not sgd.acc.abs().any().item()
+    sgd.close()
+
+
+def test_delayed_accumulation_period_one_is_a_double_step(dev):
+    """With one tile and T = 1 the buffer holds exactly the location's own
+    gradient, so each location takes two steps of alpha on the same gradient:
+    the same iterates as per-location descent with step 2 alpha."""
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300.sgd import SequentialGD
+    wl = synth.workload_random(64, 3, 2, 3, 9, seed=92, amp_jitter=0.1)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    obj0 = start_object(wl, "perturbed", 6)
+    g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    pos, meas = to_dev(wl.pos, torch.int32, dev), to_dev(I, torch.float32, dev)
+    out = []
+    for period, a in ((1, 3e-3), (0, 6e-3)):
+        sgd = SequentialGD(g, 1, dev, period=period)
+        P, O = to_dev(wl.probe, torch.complex64, dev), to_dev(obj0, torch.complex64, dev)
+        sgd.epoch(pos, P, O, meas, a, 0.0)
+        out.append(O.cpu().numpy())
+        sgd.close()
+    assert rel_l2(out[0], out[1]) <= 1e-6
+
+
+def test_delayed_accumulation_convergence_by_period(dev):
+    """The paper's question of how often to communicate (Sec. VI-F, Fig. 9):
+    loss against epochs for T = 1, N/8 and N on a 64-position block of the
+    576-position multislice workload (16 slices of 384^2, Poisson data), with
+    per-location steps.  Every schedule lowers the cost every epoch."""
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300.sgd import SequentialGD
+    wl = synth.workload_multislice()
+    wl.pos = wl.pos.reshape(24, 24, 2)[8:16, 8:16].reshape(-1, 2).copy()
+    I = measurements(wl, counts_seed=1002)
+    obj0 = start_object(wl, "perturbed", 9)
+    g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    pos, meas = to_dev(wl.pos, torch.int32, dev), to_dev(I, torch.float32, dev)
+    full = api.Plan(g, dev)
+    _, g0, _ = full.loss_grad(pos, to_dev(wl.probe, torch.complex64, dev), to_dev(obj0, torch.complex64, dev),
+                              meas, want_probe=False)
+    a = 0.05 / float(g0.abs().max())  # a full-batch step moves O by at most 5 %
+    curves = {}
+    for T in (1, wl.N // 8, wl.N):
+        sgd = SequentialGD(g, 1, dev, period=T)
+        P, O = to_dev(wl.probe, torch.complex64, dev), to_dev(obj0, torch.complex64, dev)
+        F = [full.loss_grad(pos, P, O, meas, want_obj=False, want_probe=False)[0].item()]
+        for _ in range(3):
+            sgd.epoch(pos, P, O, meas, a, 0.0)
+            F.append(full.loss_grad(pos, P, O, meas, want_obj=False, want_probe=False)[0].item())
+        curves[T] = F
+        sgd.close()
+    full.close()
+    for T, F in curves.items():
+        print(f"T = {T:3d}: F per epoch " + " ".join(f"{f:.6e}" for f in F))
+        assert all(b < a for a, b in zip(F, F[1:])), (T, F)

@@ -7,8 +7,10 @@ of the forward chain, amplified by the amplitude residual, puts the gradient
 error of any FP32 evaluation near 1e-5..3e-5; there the bar is 1.5x the error
 of a SciPy single-precision evaluation of the same chain on the same inputs
 (tests/helpers.fp32_chain_loss_grad), so the kernel must be as accurate as a
-plain FP32 implementation.  Where the oracle's loss is 0 (noise-free data at
-the true object) the check is absolute: F_gpu <= 1e-6 * sum(I).
+plain FP32 implementation (the loss bar likewise, where that model's loss
+error exceeds 1e-5: the 100-slice chain of 1024^2 windows).  Where the
+oracle's loss is 0 (noise-free data at the true object) the check is
+absolute: F_gpu <= 1e-6 * sum(I).
 """
 import numpy as np
 import pytest
@@ -53,13 +55,15 @@ def _check(wl, obj, I, dev, tol=TOL_FP32, fp32_floor=False, **kw):
     l, go, gp = _run(wl, obj, I, dev, **kw)
     el = abs(l - L) / abs(L)
     eo, ep = rel_l2(go, gO), rel_l2(gp, gP)
-    tol_o = tol_p = tol
+    tol_l = tol_o = tol_p = tol
     if fp32_floor:
-        _, fo, fp = fp32_chain_loss_grad(wl.probe, obj, wl.pos, I, h)
+        lf, fo, fp = fp32_chain_loss_grad(wl.probe, obj, wl.pos, I, h)
+        tol_l = max(tol, 1.5 * abs(lf - L) / abs(L))
         tol_o = max(tol, 1.5 * rel_l2(fo, gO))
         tol_p = max(tol, 1.5 * rel_l2(fp, gP))
-    print(f"{wl.name}: loss {el:.2e} gO {eo:.2e} (bar {tol_o:.1e}) gP {ep:.2e} (bar {tol_p:.1e})")
-    assert el <= tol and eo <= tol_o and ep <= tol_p, (el, eo, ep)
+    print(f"{wl.name}: loss {el:.2e} (bar {tol_l:.1e}) gO {eo:.2e} (bar {tol_o:.1e}) gP {ep:.2e} "
+          f"(bar {tol_p:.1e})")
+    assert el <= tol_l and eo <= tol_o and ep <= tol_p, (el, eo, ep)
     return l, go, gp
 
 
@@ -357,8 +361,53 @@ def test_recompute_mode_matches_store_all(dev, M, S, L):
     K = -(-S // L)
     per = wl.M * wl.M * 8
     assert p_all.workspace_bytes // wl.N == (2 * S - 1) * per + per + 8
-    assert p_rc.workspace_bytes // wl.N == (S + K - 1 + L + 1) * per + per + 8
+    assert p_rc.workspace_bytes // wl.N == (K + L - 1) * per + per + 8
     p_all.close()
+    p_rc.close()
+
+
+@pytest.mark.parametrize("M", [64, 128])
+def test_recompute_workspace_does_not_hold_a_patch_per_slice(dev, M):
+    """Per-position workspace in recompute mode is K - 2 checkpoints, one
+    segment of L waves, the parked adjoint state and the probe gradient:
+    for a fixed segment length it grows only by the checkpoints, never by a
+    buffer per slice, and with the automatic choice (K = L = sqrt(S)) it is
+    2 sqrt(S) buffers against 2S when every wave is kept."""
+    from paper_2205_06327_gb300 import api
+    per = M * M * 8
+    for S, L in [(16, 4), (64, 4), (64, 8), (100, 10), (30, 5)]:
+        g = api.Geometry(M, S, M + 8, M + 8, 4, 0.0251, 2.0, 0.1)
+        p = api.Plan(g, dev, ckpt_every=L)
+        K = -(-S // L)
+        assert p.workspace_bytes // 4 == (K + L - 1) * per + per + 8, (S, L)
+        p.close()
+    for S in (16, 64):
+        g = api.Geometry(M, S, M + 8, M + 8, 4, 0.0251, 2.0, 0.1)
+        auto, full = api.Plan(g, dev, ckpt_every="auto"), api.Plan(g, dev)
+        r = int(np.ceil(np.sqrt(S)))
+        assert auto.workspace_bytes // 4 == 2 * r * per + 8
+        assert full.workspace_bytes // 4 == 2 * S * per + 8
+        auto.close()
+        full.close()
+
+
+@pytest.mark.parametrize("M,S,L", [(96, 7, 3), (48, 5, 2), (192, 4, 1)])
+def test_recompute_mode_generic_windows(dev, M, S, L):
+    """The generic-window path in recompute mode: the same forward and adjoint
+    operations in the same order as when every wave is kept, so the loss and
+    both gradients are bit-identical; the workspace holds K - 2 checkpoints,
+    one segment's waves and exit-wave gradients, the parked state, the wave
+    buffer and the probe gradient."""
+    wl = synth.workload_random(M, S, 2, 3, 9, seed=60 + M + S, amp_jitter=0.1)
+    I = (measurements(wl) * 1.3).astype(np.float32)
+    obj = start_object(wl, "perturbed", 8)
+    ref = _run(wl, obj, I, dev)
+    rc = _check(wl, obj, I, dev, ckpt_every=L)
+    assert rc[0] == ref[0] and np.array_equal(rc[1], ref[1]) and np.array_equal(rc[2], ref[2])
+    p_rc = _plan(wl, dev, ckpt_every=L)
+    K = -(-S // L)
+    per = M * M * 8
+    assert p_rc.workspace_bytes // wl.N == (K + 2 * L + 1) * per + 8
     p_rc.close()
 
 
@@ -478,8 +527,8 @@ def test_fp16x3_random_problems(dev, S):
 
 
 def test_fp16x3_multislice_workload(dev):
+    """The split-precision workload at full size: all 576 positions, 16 slices."""
     wl = synth.workload_multislice()
-    wl.pos = wl.pos[::4]
     I = measurements(wl, counts_seed=1002)
     _check(wl, start_object(wl, "perturbed", 2), I, dev, tol=TOL_FP16X3, precision="fp16x3")
 
@@ -533,6 +582,45 @@ def test_paper_scale_window_1024(dev):
     wl = synth.workload_random(1024, 2, 1, 2, 200, seed=98, amp_jitter=0.1)
     I = (measurements(wl) * 1.1).astype(np.float32)
     _check(wl, start_object(wl, "perturbed", 2), I, dev)
+
+
+def _paper_scale_problem(S, n_pos):
+    """Table I's detector (1024^2) and slice count (100): a smooth random phase
+    object (band-limited noise, 0.3 rad per slice; vectorised, unlike the atom
+    splatting of the other workloads, which would take minutes at this size),
+    the defocused probe of the random workloads, positions 8 px apart."""
+    M = 1024
+    g = synth.rng(2048 + S)
+    H, W = M + 8 * (n_pos - 1) + 2, M + 16 * (n_pos - 1) + 3
+    ky = np.fft.fftfreq(H)[:, None]
+    kx = np.fft.fftfreq(W)[None, :]
+    lowpass = np.exp(-(ky ** 2 + kx ** 2) / (2 * 0.02 ** 2))
+    obj = np.empty((S, H, W), np.complex64)
+    for s in range(S):
+        ph = np.fft.ifft2(np.fft.fft2(g.standard_normal((H, W))) * lowpass).real
+        obj[s] = np.exp(1j * 0.3 * ph / np.abs(ph).max())
+    probe = synth.defocused_probe(M, 0.15, np.pi * 0.15 * M, 1.0, energy=float(M))
+    pos = np.array([[8 * i, 16 * i] for i in range(n_pos)], np.int32)
+    return synth.Workload(f"paper-scale M={M} S={S}", M, S, H, W, pos, probe, obj)
+
+
+@pytest.mark.slow
+def test_paper_scale_window_1024_100_slices_recompute(dev):
+    """Table I's shape per position: 1024^2 windows through 100 slices, in
+    recompute mode (auto: 10 checkpoints, segments of 10), two positions,
+    against the FP64 oracle.  The 100-slice chain of 1024^2 transforms sits at
+    the FP32 rounding floor (the far field carries about 1e-5 of rounding,
+    which the amplitude residual amplifies in the loss and the gradients), so
+    the bars are the plain-FP32 model's errors on the same inputs."""
+    wl = _paper_scale_problem(100, 2)
+    h = propagator(wl)
+    obj = c64(wl.obj)
+    I = (orc.intensities(c64(wl.probe), obj, wl.pos, h) * 1.1).astype(np.float32)
+    plan = _plan(wl, dev, ckpt_every="auto")
+    per = 1024 * 1024 * 8
+    assert plan.workspace_bytes // wl.N == (10 + 2 * 10 + 1) * per + 8
+    plan.close()
+    _check(wl, obj, I, dev, fp32_floor=True, ckpt_every="auto")
 
 
 def test_generic_window_more_positions_than_a_chunk(dev):
