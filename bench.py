@@ -534,8 +534,9 @@ def run_gpu(args, world, rank, local, pool):
         wl.pos = wl.pos[: args.positions]
     if args.order == "shuffled":
         wl.pos = wl.pos[np.random.default_rng(12345).permutation(len(wl.pos))]
-    if args.ckpt_every is None:  # the PbTiO3-shaped workload recomputes waves in the adjoint:
-        args.ckpt_every = 5 if args.config == 3 else 0  # ceil(sqrt(30)) = 6 checkpoints, interval 5
+    if args.ckpt_every is None:  # the PbTiO3-shaped and paper-scale workloads recompute waves in
+        # the adjoint: ceil(sqrt(S)) checkpoints, so every 5 of 30 and every 10 of 100 slices
+        args.ckpt_every = {3: 5, 6: 10}.get(args.config, 0)
     m = measure_workload(wl, args.config, args, device, world, rank, local, args.ckpt_every, args.steps,
                          args.warmup, f"{args.clocks_csv}.r{rank}.csv" if args.clocks_csv else None)
     pos, probe, obj, I, gO, gP = m["tensors"]
@@ -724,8 +725,9 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5],
-                    help="workload: 1 single slice, 2 multislice (default), 3 PbTiO3-shaped, 5 batched uneven")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5, 6],
+                    help="workload: 1 single slice, 2 multislice (default), 3 PbTiO3-shaped, 5 batched uneven, "
+                         "6 the paper's per-position shape (1024^2 window, 100 slices) on 8 positions")
     ap.add_argument("--iterations", type=int, default=50, help="gradient-descent iterations (workload 5)")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=576)
@@ -756,8 +758,10 @@ def main(argv=None):
         return run_multi(args, world, rank, local)
     pool = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # spawn the oracle's workers before the first CUDA call
-        pool = OraclePool(args.config, os.cpu_count() or 1)
+        # spawn the oracle's workers before the first CUDA call (no more than
+        # the sample has positions: each worker holds the workload)
+        n_pos = 8 if args.config == 6 else args.cpu_sample  # workload 6 has 8 positions
+        pool = OraclePool(args.config, max(1, min(os.cpu_count() or 1, n_pos, args.cpu_sample)))
     try:
         return run_gpu(args, world, rank, local, pool)
     finally:

@@ -190,6 +190,29 @@ def workload_perovskite(seed: int = SEED_BASE + 3, n_rows: int = 126,
                     pixel_A=px, potential=V, counts=1.0e5)
 
 
+def workload_paper_scale(S: int = 100, n_pos: int = 8, seed: int = SEED_BASE + 6) -> Workload:
+    """The paper's per-position shape (Table I: 1024^2 detector, 100 slices) on
+    a short diagonal scan: positions 8 px apart in y and 16 px in x, a smooth
+    random phase object (band-limited Gaussian noise scaled to 0.3 rad per
+    slice; generated with FFTs, unlike the atom splatting above, which would
+    take minutes at this size), the defocused probe of :func:`workload_random`.
+    Noise-free data (the caller scales or perturbs them)."""
+    M = 1024
+    g = rng(seed)
+    H, W = M + 8 * (n_pos - 1) + 2, M + 16 * (n_pos - 1) + 3
+    ky = np.fft.fftfreq(H)[:, None]
+    kx = np.fft.fftfreq(W)[None, :]
+    lowpass = np.exp(-(ky ** 2 + kx ** 2) / (2 * 0.02 ** 2))
+    obj = np.empty((S, H, W), np.complex64)
+    for s in range(S):
+        ph = np.fft.ifft2(np.fft.fft2(g.standard_normal((H, W))) * lowpass).real
+        obj[s] = np.exp(1j * 0.3 * ph / np.abs(ph).max())
+    probe = defocused_probe(M, 0.15, np.pi * 0.15 * M, 1.0, energy=float(M))
+    pos = np.array([[8 * i, 16 * i] for i in range(n_pos)], np.int32)
+    return Workload(f"paper-scale 1024^2 window, {S} x {H}x{W} object, {n_pos} positions", M, S, H, W, pos,
+                    probe, obj)
+
+
 def workload_random(M: int, S: int, ny: int, nx: int, step: int, seed: int,
                     max_phase: float = 0.3, amp_jitter: float = 0.0,
                     counts: float | None = None) -> Workload:
@@ -220,13 +243,16 @@ def workload_random(M: int, S: int, ny: int, nx: int, step: int, seed: int,
 
 
 def workload(config_id: int) -> Workload:
-    """The five workload shapes by number (1: single slice ... 3: PbTiO3-shaped)."""
+    """The workload shapes by number (1: single slice, 2/4: multislice,
+    3: PbTiO3-shaped, 6: the paper's per-position shape on 8 positions)."""
     if config_id == 1:
         return workload_single_slice()
     if config_id in (2, 4):
         return workload_multislice()
     if config_id == 3:
         return workload_perovskite()
+    if config_id == 6:
+        return workload_paper_scale()
     raise ValueError(f"no workload {config_id}")
 
 

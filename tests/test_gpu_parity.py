@@ -584,26 +584,6 @@ def test_paper_scale_window_1024(dev):
     _check(wl, start_object(wl, "perturbed", 2), I, dev)
 
 
-def _paper_scale_problem(S, n_pos):
-    """Table I's detector (1024^2) and slice count (100): a smooth random phase
-    object (band-limited noise, 0.3 rad per slice; vectorised, unlike the atom
-    splatting of the other workloads, which would take minutes at this size),
-    the defocused probe of the random workloads, positions 8 px apart."""
-    M = 1024
-    g = synth.rng(2048 + S)
-    H, W = M + 8 * (n_pos - 1) + 2, M + 16 * (n_pos - 1) + 3
-    ky = np.fft.fftfreq(H)[:, None]
-    kx = np.fft.fftfreq(W)[None, :]
-    lowpass = np.exp(-(ky ** 2 + kx ** 2) / (2 * 0.02 ** 2))
-    obj = np.empty((S, H, W), np.complex64)
-    for s in range(S):
-        ph = np.fft.ifft2(np.fft.fft2(g.standard_normal((H, W))) * lowpass).real
-        obj[s] = np.exp(1j * 0.3 * ph / np.abs(ph).max())
-    probe = synth.defocused_probe(M, 0.15, np.pi * 0.15 * M, 1.0, energy=float(M))
-    pos = np.array([[8 * i, 16 * i] for i in range(n_pos)], np.int32)
-    return synth.Workload(f"paper-scale M={M} S={S}", M, S, H, W, pos, probe, obj)
-
-
 @pytest.mark.slow
 def test_paper_scale_window_1024_100_slices_recompute(dev):
     """Table I's shape per position: 1024^2 windows through 100 slices, in
@@ -612,7 +592,7 @@ def test_paper_scale_window_1024_100_slices_recompute(dev):
     the FP32 rounding floor (the far field carries about 1e-5 of rounding,
     which the amplitude residual amplifies in the loss and the gradients), so
     the bars are the plain-FP32 model's errors on the same inputs."""
-    wl = _paper_scale_problem(100, 2)
+    wl = synth.workload_paper_scale(100, 2)
     h = propagator(wl)
     obj = c64(wl.obj)
     I = (orc.intensities(c64(wl.probe), obj, wl.pos, h) * 1.1).astype(np.float32)
