@@ -370,8 +370,9 @@ def measure_workload(wl, config_id, args, device, world, rank, local, ckpt_every
     obj0 = start_object(wl)
     geom = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
     tile = (0, 0)
+    ws = int(args.workspace_mb) << 20
     plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=ckpt_every,
-                    precision=args.precision)
+                    precision=args.precision, workspace_bytes=ws)
     pos = torch.from_numpy(wl.pos).to(device)
     probe = torch.from_numpy(wl.probe.astype(np.complex64)).to(device)
     obj_true = torch.from_numpy(wl.obj.astype(np.complex64)).to(device)
@@ -394,7 +395,7 @@ def measure_workload(wl, config_id, args, device, world, rank, local, ckpt_every
                                   use_cache=False, ckpt_every=ckpt_every)
         plan.close()
         plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=ckpt_every,
-                        precision=args.precision)
+                        precision=args.precision, workspace_bytes=ws)
     gO = torch.empty((wl.S, wl.H, wl.W), dtype=torch.complex64, device=device)
     gP = torch.empty((wl.M, wl.M), dtype=torch.complex64, device=device)
     loss = torch.empty((), dtype=torch.float64, device=device)
@@ -506,7 +507,8 @@ def parity_sample(wl, args, device, tile, ckpt_every, tensors, pool, k=48):
     idx = cpu_sample_indices(wl, k)
     sel = torch.from_numpy(idx).to(device)
     g = api.Geometry(wl.M, wl.S, wl.H, wl.W, len(idx), wl.lambda_A, wl.dz_A, wl.pixel_A)
-    plan = api.Plan(g, device, async_check=True, tile=tile, ckpt_every=ckpt_every, precision=args.precision)
+    plan = api.Plan(g, device, async_check=True, tile=tile, ckpt_every=ckpt_every, precision=args.precision,
+                    workspace_bytes=int(args.workspace_mb) << 20)
     L, gO, gP = plan.loss_grad(pos[sel].contiguous(), probe, obj, I[sel].contiguous())
     torch.cuda.synchronize(device)
     plan.close()
@@ -549,7 +551,7 @@ def run_gpu(args, world, rank, local, pool):
         h2d = sum(v.numel() * v.element_size() for v in hp.values())
         d2h = 8 + gO.numel() * 8 + gP.numel() * 8
         eplan = api.Plan(geom, device, async_check=True, tile=tile, ckpt_every=args.ckpt_every,
-                         precision=args.precision)
+                         precision=args.precision, workspace_bytes=int(args.workspace_mb) << 20)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
         # warm-up as in the timed loop: the previous results stay alive while
         # the next call runs, so the pinned result buffers are all allocated
@@ -737,6 +739,9 @@ def main(argv=None):
                          "(the library uses the caller's order; this measures what the order costs)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "fp16x3"],
                     help="bf16x3 / fp16x3: 2-D transforms as hi/lo split DFT products on the tensor cores")
+    ap.add_argument("--workspace-mb", type=int, default=0,
+                    help="cap on the plan's workspace in MiB (0: the library's default, 8 GiB); the "
+                         "positions run in chunks that fit it")
     ap.add_argument("--ckpt-every", type=int, default=None,
                     help="recompute mode: keep a wave checkpoint every L slices (0 = keep all)")
     ap.add_argument("--windows", default="",

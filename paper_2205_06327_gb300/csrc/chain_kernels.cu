@@ -76,6 +76,21 @@ __device__ __forceinline__ void for_p2(int t, F&& f) {
 
 __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }
 
+// Recompute mode's finished patches are read once by the accumulation that
+// follows each launch: streaming stores by default; plain stores (to keep a
+// chunk's patches in L2 when the chunk is small enough) with
+// PTYCHO_PATCH_STORE_CS=0.
+#ifndef PTYCHO_PATCH_STORE_CS
+#define PTYCHO_PATCH_STORE_CS 1
+#endif
+__device__ __forceinline__ void store_patch(float2* p, float2 v) {
+#if PTYCHO_PATCH_STORE_CS
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
+
 }  // namespace
 
 template <int M, int MODE>
@@ -150,7 +165,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
       float2* seg = rc_slot(seg_slot + (s - s0));
       for_p0<C>(t, [&](int e, int py, int px) {
         const int k = py * M + px;
-        __stcs(seg + k, cconjmul(seg[k], v[e]));  // conj(psi_s) g_phi_s over psi_s
+        store_patch(seg + k, cconjmul(seg[k], v[e]));  // conj(psi_s) g_phi_s over psi_s
       });
       const float2* ow = objw + (size_t)s * HW;
       for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmulc(v[e], ldg2(ow + (size_t)py * a.W + px)); });
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
         float2* seg = rc_slot(seg_slot + (s - s0));
         for_p0<C>(t, [&](int e, int py, int px) {
           const int k = py * M + px;
-          __stcs(seg + k, cconjmul(seg[k], v[e]));  // conj(psi_s) g_phi_s over psi_s
+          store_patch(seg + k, cconjmul(seg[k], v[e]));  // conj(psi_s) g_phi_s over psi_s
         });
         const float2* ow = objw + (size_t)s * HW;
         for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmulc(v[e], ldg2(ow + (size_t)py * a.W + px)); });
