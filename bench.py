@@ -6,11 +6,15 @@ amplitude residual, exact adjoint), the tiled object-gradient accumulation,
 the probe-gradient and FP64 loss reductions.  Metric: probe positions per
 second.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1|2|3] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1|2|3|5|6] [--impl reference]
 
 Inputs are synthetic (seeded) and resident in HBM when the timed region
 starts; the L2 is flushed (512 MiB write) between timed steps, outside the
-per-step CUDA events.  ``e2e`` repeats the measurement through the public
+per-step CUDA events.  The default line is the 576-position multislice
+workload; after it, the same line carries the 16632-position PbTiO3-shaped
+workload (``paper_shaped``) and the 32 batched uneven problems under one CUDA
+graph per iteration (``batched``), and ``parity`` gives the timed path's
+errors against the FP64 oracle on 48 of the positions.  ``e2e`` repeats the measurement through the public
 Python API with host (pinned) inputs and host results, copies included (the
 call goes to ``ptycho_loss_grad_host``, which uploads the later positions'
 intensities while the first chain wave runs).
@@ -601,6 +605,18 @@ def run_gpu(args, world, rank, local, pool):
                         "gpu_launches_per_step": m3["launches_per_step"],
                         "clocks": {"sm_mhz": m3["csum"]["sm_mhz"], "reasons": m3["csum"]["reasons"]}}
 
+    # the batched workload (32 uneven problems, one CUDA graph per iteration),
+    # timed over fewer iterations than its own run
+    batched = None
+    if args.config == 2 and not args.no_batched and not args.positions:
+        mb = measure_multi(args, device, world, local, 10, 3)
+        batched = {"workload": f"{mb['problems']} uneven problems (windows 64-256, 1-24 slices), one CUDA "
+                               "graph per gradient-descent iteration",
+                   "value": mb["value"], "unit": UNIT, "ms_per_step": mb["ms_per_step"],
+                   "iterations": mb["iterations"], "positions_per_iteration": mb["positions_per_iteration"],
+                   "gpu_launches_per_step": mb["gpu_launches_per_step"], "tiles": mb["tiles"],
+                   "clocks": {"sm_mhz": mb["csum"]["sm_mhz"], "reasons": mb["csum"]["reasons"]}}
+
     csum = m["csum"]
     line = {
         "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -620,6 +636,7 @@ def run_gpu(args, world, rank, local, pool):
         "gpu_launches_per_step": m["launches_per_step"],
         "clocks": {"sm_mhz": csum["sm_mhz"], "sm_max_mhz": csum["sm_max_mhz"], "reasons": csum["reasons"]},
         "paper_shaped": paper_shaped,
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -629,7 +646,7 @@ def run_gpu(args, world, rank, local, pool):
     return 0
 
 
-def run_multi(args, world, rank, local):
+def measure_multi(args, device, world, local, iterations, warmup):
     """Batched uneven reconstructions: the 32 seeded problem shapes, each
     advanced by fixed-step gradient descent, all problems of one iteration in a
     single captured CUDA graph; the accumulation tile is tuned per window size."""
@@ -638,11 +655,6 @@ def run_multi(args, world, rank, local):
     from paper_2205_06327_gb300 import api, autotune, synth
     from paper_2205_06327_gb300.multi import MultiProblem, Problem, supported
 
-    device = torch.device("cuda", local)
-    torch.cuda.set_device(device)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=device)
     shapes = synth.multi_problem_shapes()
     probs, skipped = [], []
     windows = {int(x) for x in args.windows.split(",")} if args.windows else None
@@ -674,11 +686,10 @@ def run_multi(args, world, rank, local):
     mp = MultiProblem(probs, device, precision=args.precision)
     for pl in mp.plans:
         pl.timing(reset=True)
-    mp.capture(1e-3, 1e-6, warmup=args.warmup)
+    mp.capture(1e-3, 1e-6, warmup=warmup)
     # the library counts the kernels each call enqueues: warm-up iterations
     # plus the captured one; a replay launches the captured iteration's kernels
-    launches_per_iter = sum(pl.timing(reset=True)["launches"] for pl in mp.plans) / (args.warmup + 1)
-    iters = args.iterations
+    launches_per_iter = sum(pl.timing(reset=True)["launches"] for pl in mp.plans) / (warmup + 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(device)
     barrier(world, device)
@@ -686,7 +697,7 @@ def run_multi(args, world, rank, local):
     clocks = ClockSampler(local, None)
     with clocks:
         e0.record(stream)
-        mp.run(iters)
+        mp.run(iterations)
         e1.record(stream)
         torch.cuda.synchronize(device)
     barrier(world, device)
@@ -694,26 +705,41 @@ def run_multi(args, world, rank, local):
     t = e0.elapsed_time(e1) / 1e3
     t_max = reduce_max(t, world, device)
     per_it = mp.positions_per_iteration
-    value = world * per_it * iters / t_max
-    csum = clocks.summary()
+    out = {"value": world * per_it * iterations / t_max, "ms_per_step": t_max / iterations * 1e3,
+           "iterations": iterations, "problems": len(probs), "skipped_windows": skipped,
+           "positions_per_iteration": per_it, "tiles": {str(k): list(v) for k, v in tiles.items()},
+           "gpu_launches_per_step": launches_per_iter, "csum": clocks.summary(),
+           "final_loss_sum": float(mp.loss.sum().item())}
+    mp.close()
+    return out
+
+
+def run_multi(args, world, rank, local):
+    import torch
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    m = measure_multi(args, device, world, local, args.iterations, args.warmup)
+    csum = m["csum"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": iters, "warmup": args.warmup,
-        "ms_per_step": t_max / iters * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": m["iterations"],
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"{len(probs)} uneven problems of the 32 seeded shapes (windows 64-256, "
+        "config": {"workload": f"{m['problems']} uneven problems of the 32 seeded shapes (windows 64-256, "
                                "1-24 slices), one CUDA graph per gradient-descent iteration"
                                + (f", windows {args.windows} only" if args.windows else ""),
-                   "problems": len(probs), "skipped_windows": skipped,
-                   "positions_per_iteration": per_it, "iterations": iters,
-                   "tiles": {str(k): list(v) for k, v in tiles.items()},
+                   "problems": m["problems"], "skipped_windows": m["skipped_windows"],
+                   "positions_per_iteration": m["positions_per_iteration"], "iterations": m["iterations"],
+                   "tiles": m["tiles"],
                    "l2": "inputs larger than L2 in aggregate; no flush between graph replays"},
-        "gpu_launches": int(round(launches_per_iter * iters)),
-        "gpu_launches_per_step": launches_per_iter,
+        "gpu_launches": int(round(m["gpu_launches_per_step"] * m["iterations"])),
+        "gpu_launches_per_step": m["gpu_launches_per_step"],
         "clocks": {"sm_mhz": csum["sm_mhz"], "sm_max_mhz": csum["sm_max_mhz"], "reasons": csum["reasons"]},
-        "final_loss_sum": float(mp.loss.sum().item()),
+        "final_loss_sum": m["final_loss_sum"],
     }
-    mp.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -753,6 +779,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-paper-shaped", action="store_true",
                     help="skip the second measurement, of the 16632-position PbTiO3-shaped workload")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the third measurement, of the 32 batched uneven problems (10 iterations)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -296,8 +296,9 @@ PTYCHO_API int ptycho_plan_timing(ptycho_plan plan, ptycho_timing* out, int32_t 
  *
  * Scratch: one static device array of 64 MiB, held by every GPU that loads
  * the library until the process exits.  A fixed part (the twiddle and
- * propagator tables, 4 * M * M * 8 bytes of probe-gradient partials and a few
- * words; about 0.5 MiB at M = 128) comes first; positions then run in chunks
+ * propagator tables, among them the M * M * 8-byte full propagator,
+ * 4 * M * M * 8 bytes of probe-gradient partials and a few words; about
+ * 0.63 MiB at M = 128) comes first; positions then run in chunks
  * that fit in the rest, each position needing
  *     (2S - 1) * M * M * 8 + M * M * 8 + 8 bytes
  * (S = 253 is the deepest chain at M = 128, S = 1021 at M = 64).  A problem whose

@@ -76,6 +76,21 @@ __device__ __forceinline__ void for_p2(int t, F&& f) {
 
 __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }
 
+// The forward model's propagations multiply by the full propagator table
+// (one rounding per element fewer; the residual amplifies the forward
+// model's rounding), the adjoint's by the separable factors in shared memory.
+#ifndef PTYCHO_PROP_TABLE
+#define PTYCHO_PROP_TABLE 1
+#endif
+template <class C>
+__device__ __forceinline__ void mul_prop_fwd(float2 (&v)[C::V], const float2* hs, const float2* h2, int t) {
+#if PTYCHO_PROP_TABLE
+  mul_table<C, false>(v, h2, t);
+#else
+  mul_separable<C, false>(v, hs, t);
+#endif
+}
+
 // Recompute mode's finished patches are read once by the accumulation that
 // follows each launch: streaming stores by default; plain stores (to keep a
 // chunk's patches in L2 when the chunk is small enough) with
@@ -155,7 +170,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
         const float2* ow = objw + (size_t)s * HW;
         for_p0<C>(t, [&](int e, int py, int px) { v[e] = cmul(v[e], ldg2(ow + (size_t)py * a.W + px)); });
         fft_fwd<C>(v, sm, tw, t);
-        mul_separable<C, false>(v, hs, t);
+        mul_prop_fwd<C>(v, hs, a.h2, t);
         fft_inv<C>(v, sm, tw, t);
       }
     }
@@ -217,7 +232,7 @@ __global__ void __launch_bounds__(Cfg<M>::T, Cfg<M>::MIN_BLOCKS) k_chain(const C
     });
     if (s < a.S - 1) {
       fft_fwd<C>(v, sm, tw, t);
-      mul_separable<C, false>(v, hs, t);
+      mul_prop_fwd<C>(v, hs, a.h2, t);
       fft_inv<C>(v, sm, tw, t);
     }
   }

@@ -364,4 +364,32 @@ __device__ __forceinline__ void mul_separable(float2 (&v)[C::V], const float2* _
   });
 }
 
+// Multiply the spectrum (pass-2 grouping) by the propagator read from a full
+// M x M table h2[ky][kx] (FFT order), each entry rounded once from FP64: one
+// rounding per element fewer than forming h(ky) h(kx) here.  The table is
+// read through the read-only cache (the same 64 or 128 KiB for every block).
+template <class C, bool CONJ>
+__device__ __forceinline__ void mul_table(float2 (&v)[C::V], const float2* __restrict__ h2, int t) {
+  using P = PassShape<C, 2>;
+  t = opaque(t);
+  static_for<0, P::Q>([&](auto qq) {
+    constexpr int q = decltype(qq)::value;
+    int py, px;
+    C::template base<2>(t, q, py, px);
+    const float2* hp = h2 + freq_y<C>(py) * C::M + freq_x<C>(px);
+    float2 hh[P::G];
+    static_for<0, P::RY>([&](auto aa) {
+      constexpr int a = decltype(aa)::value;
+      static_for<0, P::RX>([&](auto bb) {
+        constexpr int b = decltype(bb)::value;
+        hh[a * P::RX + b] = __ldg(hp + a * C::ry(0) * C::ry(1) * C::M + b * C::rx(0) * C::rx(1));
+      });
+    });
+    static_for<0, P::G>([&](auto ee) {
+      constexpr int e = decltype(ee)::value;
+      v[q * P::G + e] = cmul_opt<CONJ>(v[q * P::G + e], hh[e]);
+    });
+  });
+}
+
 }  // namespace ptycho

@@ -31,6 +31,7 @@ struct ChainArgs {
   int S, H, W;
   const float2* tw;       // [M]   w_M^e = exp(-2 pi i e / M)
   const float2* hs;       // [M]   one separable factor of the propagator, times 1/M
+  const float2* h2;       // [M][M] the propagator h(ky) h(kx) / M^2 (register-resident kernels)
   int ws_n;               // positions the workspace holds (slice stride of ws_psi / ws_gphi)
   int ckpt_L;             // recompute mode: checkpoint every ckpt_L slices
   int seg;                // MODE_RC_SEG: the segment differentiated by this launch

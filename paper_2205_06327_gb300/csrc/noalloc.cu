@@ -112,6 +112,7 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
   size_t off = 0;
   float2* d_tw = reinterpret_cast<float2*>(base + off); off = align_up(off + M * sizeof(float2));
   float2* d_hs = reinterpret_cast<float2*>(base + off); off = align_up(off + M * sizeof(float2));
+  float2* d_h2 = reinterpret_cast<float2*>(base + off); off = align_up(off + MM * sizeof(float2));
   int* d_status = reinterpret_cast<int*>(base + off);   off = align_up(off + sizeof(int));
   double* d_loss = reinterpret_cast<double*>(base + off); off = align_up(off + sizeof(double));
   float2* gp_part = reinterpret_cast<float2*>(base + off); off = align_up(off + kSplit * MM * sizeof(float2));
@@ -138,6 +139,22 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
     const double f = (double)(k <= (M - 1) / 2 ? k : k - M) / ((double)M * p.pixel_A);
     const double ph = -M_PI * p.lambda_A * p.dz_A * f * f;
     hs[k] = make_float2((float)(std::cos(ph) / M), (float)(std::sin(ph) / M));
+  }
+  // The full propagator h(ky) h(kx) / M^2, staged through the stack 16 rows
+  // at a time (a copy from pageable memory returns once its source is staged).
+  for (int k0 = 0; k0 < M; k0 += 16) {
+    float2 rows[16 * 128];
+    for (int ky = k0; ky < k0 + 16; ++ky)
+      for (int kx = 0; kx < M; ++kx) {
+        const double fy = (double)(ky <= (M - 1) / 2 ? ky : ky - M) / ((double)M * p.pixel_A);
+        const double fx = (double)(kx <= (M - 1) / 2 ? kx : kx - M) / ((double)M * p.pixel_A);
+        const double ph = -M_PI * p.lambda_A * p.dz_A * (fy * fy + fx * fx);
+        rows[(ky - k0) * M + kx] =
+            make_float2((float)(std::cos(ph) / ((double)M * M)), (float)(std::sin(ph) / ((double)M * M)));
+      }
+    if ((e = cudaMemcpyAsync(d_h2 + (size_t)k0 * M, rows, 16 * M * sizeof(float2), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return noalloc_fail(PTYCHO_ERR_CUDA, cudaGetErrorString(e));
   }
   // Everything that must start at zero is cleared here: the previous call's
   // contents stay in the scratch.
@@ -167,6 +184,7 @@ extern "C" PTYCHO_API int ptycho_loss_grad_noalloc(const ptycho_params* params, 
   a.W = p.W;
   a.tw = d_tw;
   a.hs = d_hs;
+  a.h2 = d_h2;
   a.ws_n = chunk;
   a.ws_psi = ws_psi;
   a.ws_gphi = ws_gphi;

@@ -178,6 +178,7 @@ struct ptycho_plan_s {
   int64_t ws_bytes = 0;
   float2* d_tw = nullptr;     // [M]
   float2* d_hs = nullptr;     // [M]
+  float2* d_h2 = nullptr;     // [M][M] (M = 64, 128)
   float2* ws_psi = nullptr;   // [S-1][chunk][M][M] (recompute: [K-2+L+1][chunk][M][M])
   float2* ws_gphi = nullptr;  // [S][chunk][M][M] (recompute: none)
   float2* ws_gp = nullptr;    // [chunk][M][M]
@@ -230,6 +231,7 @@ void free_plan(ptycho_plan pl) {
   }
   cudaFree(pl->d_tw);
   cudaFree(pl->d_hs);
+  cudaFree(pl->d_h2);
   cudaFree(pl->ws_psi);
   cudaFree(pl->ws_gphi);
   cudaFree(pl->ws_gp);
@@ -390,6 +392,7 @@ ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe,
   a.W = pl->p.W;
   a.tw = pl->d_tw;
   a.hs = pl->d_hs;
+  a.h2 = pl->d_h2;
   a.ws_n = pl->chunk;
   a.ckpt_L = pl->ckpt_L;
   a.ws_psi = pl->ws_psi;
@@ -602,6 +605,19 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
     const double ph = -M_PI * p.lambda_A * p.dz_A * f * f;
     hs[k] = make_float2((float)(std::cos(ph) / M), (float)(std::sin(ph) / M));
   }
+  // The full propagator h(ky) h(kx) / M^2 for the register-resident kernels.
+  std::vector<float2> h2;
+  if (fused_window(M)) {
+    h2.resize((size_t)M * M);
+    for (int ky = 0; ky < M; ++ky)
+      for (int kx = 0; kx < M; ++kx) {
+        const double fy = (double)(ky <= (M - 1) / 2 ? ky : ky - M) / ((double)M * p.pixel_A);
+        const double fx = (double)(kx <= (M - 1) / 2 ? kx : kx - M) / ((double)M * p.pixel_A);
+        const double ph = -M_PI * p.lambda_A * p.dz_A * (fy * fy + fx * fx);
+        h2[(size_t)ky * M + kx] =
+            make_float2((float)(std::cos(ph) / ((double)M * M)), (float)(std::sin(ph) / ((double)M * M)));
+      }
+  }
 
   // Workspace per position in flight (gradient mode).
   const size_t MM = (size_t)M * M;
@@ -650,6 +666,7 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   rc = PTYCHO_OK;
   if (!rc) rc = dev_alloc(&pl->d_tw, M, "twiddles");
   if (!rc) rc = dev_alloc(&pl->d_hs, M, "propagator");
+  if (!rc) rc = dev_alloc(&pl->d_h2, h2.size(), "propagator table");
   if (!rc) rc = dev_alloc(&pl->ws_psi, (size_t)pl->chunk * psi_slots * MM, "wave workspace");
   if (!rc) rc = dev_alloc(&pl->ws_gphi, (size_t)pl->chunk * gphi_slots * MM, "adjoint workspace");
   if (!rc) rc = dev_alloc(&pl->ws_gp, (size_t)pl->chunk * MM, "probe-gradient workspace");
@@ -689,6 +706,8 @@ int ptycho_plan_create(ptycho_plan* out, const ptycho_params* params) {
   pl->ws_bytes = (int64_t)pl->chunk * (int64_t)per_pos;
   if ((e = cudaMemcpy(pl->d_tw, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(pl->d_hs, hs.data(), M * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!h2.empty() &&
+       (e = cudaMemcpy(pl->d_h2, h2.data(), h2.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(pl->d_scal, 0, 8 * sizeof(double))) != cudaSuccess) {
     free_plan(pl);
