@@ -279,7 +279,7 @@ def barrier(world: int, device=None):
 # arms
 # --------------------------------------------------------------------------
 
-CHAIN_SOURCES = {"fp32": ("chain_kernels.cu", "fft2d.cuh"), "bf16x3": ("chain_tc.cu", "tc_bf16.cuh"),
+CHAIN_SOURCES = {"fp32": ("chain_kernels.cu", "chain_body.inc", "fft2d.cuh"), "bf16x3": ("chain_tc.cu", "tc_bf16.cuh"),
                  "fp16x3": ("chain_tc.cu", "tc_bf16.cuh")}
 
 

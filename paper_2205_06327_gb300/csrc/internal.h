@@ -47,7 +47,20 @@ struct ChainArgs {
   int selftest_timeout;   // PTYCHO_FLAG_SELFTEST_TIMEOUT: the split-product kernel issues no MMAs
 };
 
+// Gradient-mode chains of several problems (same window M = 64 or 128, FP32,
+// every wave kept) in one launch: a[p] is problem p's ChainArgs for its
+// current chunk, whose blocks are [start[p], start[p + 1]).  Passed by value
+// as the kernel's parameter (kMultiChainMax entries keep it under 4 KB).
+constexpr int kMultiChainMax = 16;
+struct MultiChainArgs {
+  int n;
+  int start[kMultiChainMax + 1];
+  ChainArgs a[kMultiChainMax];
+};
+static_assert(sizeof(MultiChainArgs) <= 4096, "kernel parameters of the multi-problem chain exceed 4 KB");
+
 // chain_kernels.cu
+cudaError_t launch_chain_multi(int M, const MultiChainArgs& m, cudaStream_t st);
 int chain_threads(int M);
 int chain_blocks_per_sm(int M);  // resident gradient-mode blocks per SM (0 if unknown)
 size_t chain_smem_bytes(int M);

@@ -2,6 +2,7 @@
 // orchestration of the per-chunk kernel sequence.  See include/ptycho.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -402,6 +403,33 @@ ChainArgs base_args(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe,
   a.status = pl->d_status;
   a.selftest_timeout = (pl->p.flags & PTYCHO_FLAG_SELFTEST_TIMEOUT) ? 1 : 0;
   return a;
+}
+
+// Object-gradient accumulation (every wave kept) of positions
+// [c0 + off, c0 + off + n) of the current chunk, whose workspace slots start
+// at off.
+int accum_part(ptycho_plan pl, const int32_t* pos, const ptycho_c64* probe, float2* grad_obj, int c0, int off,
+               int n, int accumulate, cudaStream_t st) {
+  const ptycho_params& p = pl->p;
+  const size_t MM = (size_t)p.M * p.M;
+  AccumArgs g{};
+  g.pos = reinterpret_cast<const int2*>(pos);
+  g.pos_begin = c0 + off;
+  g.n_pos = n;
+  g.M = p.M;
+  g.S = p.S;
+  g.H = p.H;
+  g.W = p.W;
+  g.tile_h = p.tile_h ? p.tile_h : kDefaultTile;
+  g.tile_w = p.tile_w ? p.tile_w : kDefaultTile;
+  g.probe = reinterpret_cast<const float2*>(probe);
+  g.ws_n = pl->chunk;
+  g.ws_psi = pl->ws_psi + (size_t)off * MM;
+  g.ws_gphi = pl->ws_gphi + (size_t)off * MM;
+  g.grad_obj = grad_obj;
+  g.accumulate = accumulate;
+  TIMED(K_ACCUM, 1, launch_accum_obj_grad(g, st));
+  return PTYCHO_OK;
 }
 
 // F (and optionally gradients) at (probe + probe_step*probe_dir, obj + obj_step*obj_dir);
@@ -897,6 +925,112 @@ int run_multi(const ptycho_problem* probs, int32_t n, F&& fn) {
   return PTYCHO_OK;
 }
 
+// Problems whose chains the multi-problem launch takes: FP32, M = 64 or 128,
+// every wave kept, at least one position.
+bool fusable(ptycho_plan pl) {
+  return pl->p.precision == PTYCHO_FP32 && fused_window(pl->p.M) && pl->ckpt_L == 0 && !pl->wv && pl->p.N > 0;
+}
+
+// The batched workload's register-resident problems, one iteration: for each
+// window (64, 128), round r launches the chains of chunk r of every problem
+// that has one in a single kernel (up to kMultiChainMax problems per launch),
+// then runs each problem's reductions of that chunk exactly as its own call
+// would (the same kernels, inputs and summation order, so the results are
+// bit-identical to the single-problem calls).  With `step`, the gradients go
+// to the plans' step buffers and the fixed-step update follows.
+int run_multi_fused(const ptycho_problem* probs, const std::vector<int>& idx, bool step, double a_o, double a_p,
+                    cudaStream_t st) {
+  struct Item {
+    int i;
+    ptycho_plan pl;
+    float2* gO;
+    float2* gP;
+  };
+  std::vector<Item> items;
+  for (int i : idx) {
+    const ptycho_problem& q = probs[i];
+    ptycho_plan pl = q.plan;
+    const ptycho_params& p = pl->p;
+    auto tag = [&](int rc) {
+      g_last_error = "problem " + std::to_string(i) + ": " + g_last_error;
+      return rc;
+    };
+    int rc;
+    if ((rc = check_array(q.probe, "probe", true)) || (rc = check_array(q.obj, "obj", true)) ||
+        (rc = check_array(q.meas_I, "meas_I", true)) || (!step && (rc = check_array(q.grad_obj, "grad_obj", false))) ||
+        (!step && (rc = check_array(q.grad_probe, "grad_probe", false))))
+      return tag(rc);
+    if ((rc = check_positions(pl, q.pos_yx, st))) return tag(rc);
+    float2 *gO = reinterpret_cast<float2*>(q.grad_obj), *gP = reinterpret_cast<float2*>(q.grad_probe);
+    if (step) {
+      const size_t nO = (size_t)p.S * p.H * p.W, nP = (size_t)p.M * p.M;
+      if (!pl->g_obj && (rc = dev_alloc(&pl->g_obj, nO, "step object gradient"))) return tag(rc);
+      if (!pl->g_probe && (rc = dev_alloc(&pl->g_probe, nP, "step probe gradient"))) return tag(rc);
+      gO = pl->g_obj;
+      gP = pl->g_probe;
+    }
+    items.push_back({i, pl, gO, gP});
+  }
+  for (int M : {64, 128}) {
+    std::vector<Item> grp;
+    for (const Item& it : items)
+      if (it.pl->p.M == M) grp.push_back(it);
+    for (int r = 0;; ++r) {
+      std::vector<const Item*> live;
+      for (const Item& it : grp)
+        if ((int64_t)r * it.pl->chunk < it.pl->p.N) live.push_back(&it);
+      if (live.empty()) break;
+      for (size_t k0 = 0; k0 < live.size(); k0 += kMultiChainMax) {
+        const size_t k1 = std::min(live.size(), k0 + (size_t)kMultiChainMax);
+        MultiChainArgs m{};
+        m.n = (int)(k1 - k0);
+        for (size_t k = k0; k < k1; ++k) {
+          const Item& it = *live[k];
+          const ptycho_problem& q = probs[it.i];
+          const int c0 = r * it.pl->chunk, n = std::min(it.pl->chunk, it.pl->p.N - c0);
+          ChainArgs a = base_args(it.pl, q.pos_yx, q.probe, q.obj, q.meas_I);
+          a.pos_begin = c0;
+          a.n_pos = n;
+          m.a[k - k0] = a;
+          m.start[k - k0 + 1] = m.start[k - k0] + n;
+          it.pl->tm.chain_positions += n;
+        }
+        ptycho_plan pl = live[k0]->pl;  // the launch is counted (and timed) on its first problem's plan
+        TIMED(K_CHAIN, 1, launch_chain_multi(M, m, st));
+      }
+      for (const Item* it : live) {
+        ptycho_plan pl = it->pl;
+        const ptycho_problem& q = probs[it->i];
+        const int c0 = r * pl->chunk, n = std::min(pl->chunk, pl->p.N - c0);
+        if (it->gO) {
+          // the single call's split: full chain waves, then the partial last wave
+          const int tail = (pl->side && pl->wave > 0 && n > pl->wave) ? n % pl->wave : 0;
+          int rc;
+          if ((rc = accum_part(pl, q.pos_yx, q.probe, it->gO, c0, 0, n - tail, r > 0, st))) return rc;
+          if (tail && (rc = accum_part(pl, q.pos_yx, q.probe, it->gO, c0, n - tail, tail, 1, st))) return rc;
+        }
+        if (it->gP)
+          TIMED(K_PROBE, 2, launch_probe_grad(pl->ws_gp, n, pl->p.M, pl->gp_part, kProbeSplit, it->gP, r > 0, st));
+        TIMED(K_OTHER, 1, launch_loss_accum(pl->loss_part, n, pl->d_scal, r > 0, st));
+      }
+    }
+  }
+  for (const Item& it : items) {
+    ptycho_plan pl = it.pl;
+    const ptycho_problem& q = probs[it.i];
+    int rc;
+    if ((rc = deliver_loss(pl, 0, q.loss_out, st))) return rc;
+    if (step) {
+      const ptycho_params& p = pl->p;
+      TIMED(K_OTHER, 1, launch_axpy(reinterpret_cast<float2*>(q.obj), pl->g_obj, reinterpret_cast<float2*>(q.obj),
+                                    -a_o, (size_t)p.S * p.H * p.W, st));
+      TIMED(K_OTHER, 1, launch_axpy(reinterpret_cast<float2*>(q.probe), pl->g_probe,
+                                    reinterpret_cast<float2*>(q.probe), -a_p, (size_t)p.M * p.M, st));
+    }
+  }
+  return PTYCHO_OK;
+}
+
 // ptycho_loss_grad_host: host arrays in and out.  The inputs are staged in
 // plan-owned device buffers; the intensities of all but the first chain wave
 // go up on the copy stream while that wave runs.
@@ -1043,19 +1177,33 @@ int ptycho_step_accumulate(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* 
 int ptycho_multi_loss_grad(const ptycho_problem* problems, int32_t n, void* stream) {
   g_last_error.clear();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return run_multi(problems, n, [&](const ptycho_problem& q) {
+  std::vector<int> fused;
+  int rc = run_multi(problems, n, [&](const ptycho_problem& q) {
+    if (fusable(q.plan)) {
+      fused.push_back((int)(&q - problems));
+      return PTYCHO_OK;
+    }
     return loss_grad_impl(q.plan, q.pos_yx, q.probe, q.obj, q.meas_I, q.loss_out, q.grad_obj, q.grad_probe, st);
   });
+  return rc ? rc : run_multi_fused(problems, fused, false, 0.0, 0.0, st);
 }
 
 int ptycho_multi_step(const ptycho_problem* problems, int32_t n, double alpha_obj, double alpha_probe,
                       void* stream) {
   g_last_error.clear();
+  if (!std::isfinite(alpha_obj) || !std::isfinite(alpha_probe))
+    return fail(PTYCHO_ERR_ARG, "step sizes must be finite");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return run_multi(problems, n, [&](const ptycho_problem& q) {
+  std::vector<int> fused;
+  int rc = run_multi(problems, n, [&](const ptycho_problem& q) {
+    if (fusable(q.plan)) {
+      fused.push_back((int)(&q - problems));
+      return PTYCHO_OK;
+    }
     return step_impl(q.plan, q.pos_yx, q.probe, q.obj, q.meas_I, alpha_obj, alpha_probe, 0, q.loss_out, nullptr,
                      st);
   });
+  return rc ? rc : run_multi_fused(problems, fused, true, alpha_obj, alpha_probe, st);
 }
 
 int ptycho_potential_to_transmission(const float* V, ptycho_c64* obj, int64_t n, double sigma, void* stream) {

@@ -162,6 +162,28 @@ def test_multi_loss_grad_matches_single_calls(dev):
     mp.close()
 
 
+def test_multi_call_many_problems_several_chunks_matches_single_calls(dev):
+    """Eighteen register-resident problems (more than one multi-problem chain
+    launch takes) whose positions run in several chunks: the multi-problem
+    call launches each round's chains of all problems together and must still
+    give every problem's single-call results bit for bit."""
+    from paper_2205_06327_gb300.multi import MultiProblem
+    specs = [(64 if k % 2 else 128, 1 + k % 3, 2, 2 + k % 3, 9 + k) for k in range(18)]
+    probs, _ = _problems(dev, specs)
+    # about three positions per chunk for the deepest 128-window problems
+    mp = MultiProblem(probs, dev, workspace_bytes=18 * (3 * 6 * 128 * 128 * 8))
+    assert max(-(-p.geom.N // pl.chunk) for p, pl in zip(probs, mp.plans)) >= 2
+    loss, grads = mp.loss_grad_all()
+    torch.cuda.synchronize()
+    mp.check_status()
+    for i, (p, plan) in enumerate(zip(probs, mp.plans)):
+        l1, go, gp = plan.loss_grad(p.pos, p.probe, p.obj, p.meas)
+        torch.cuda.synchronize()
+        assert l1.item() == loss[i].item()
+        assert torch.equal(go, grads[i][0]) and torch.equal(gp, grads[i][1])
+    mp.close()
+
+
 def test_multi_call_argument_errors(dev):
     from paper_2205_06327_gb300 import _lib
     from paper_2205_06327_gb300.multi import MultiProblem
