@@ -526,6 +526,24 @@ def test_fp16x3_random_problems(dev, S):
     _check(wl, start_object(wl, "perturbed", 7), I, dev, tol=TOL_FP16X3, precision="fp16x3")
 
 
+def test_split_precision_memory_bounded_by_the_workspace_cap(dev):
+    """The split precisions keep every wave (no recompute mode), so their
+    memory is bounded by the workspace cap through chunking: with room for
+    three positions, 12 positions run in chunks of 3 and give the unchunked
+    results to reassociation of the chunk sums, within the split bar."""
+    wl = synth.workload_random(128, 3, 3, 4, 13, seed=71, amp_jitter=0.1)
+    I = (measurements(wl) * 1.2).astype(np.float32)
+    obj = start_object(wl, "perturbed", 8)
+    per = (2 * wl.S) * 128 * 128 * 8 + 8
+    small = _plan(wl, dev, precision="fp16x3", workspace_bytes=3 * per)
+    assert small.chunk == 3 and small.workspace_bytes <= 3 * per
+    small.close()
+    ref = _run(wl, obj, I, dev, precision="fp16x3")
+    chunked = _check(wl, obj, I, dev, tol=TOL_FP16X3, precision="fp16x3", workspace_bytes=3 * per)
+    assert abs(chunked[0] - ref[0]) <= 1e-6 * abs(ref[0])
+    assert rel_l2(chunked[1], ref[1]) <= 1e-6 and rel_l2(chunked[2], ref[2]) <= 1e-6
+
+
 def test_fp16x3_multislice_workload(dev):
     """The split-precision workload at full size: all 576 positions, 16 slices."""
     wl = synth.workload_multislice()
