@@ -257,8 +257,6 @@ struct GmLineArgs {
   int pre;    // forward transmission on load: [store psi_s], times O_s[window]
   int post;   // adjoint transmission on store: store g_phi_s, times conj(O_s[window])
   int store;  // with pre: keep psi_s in the workspace
-  int psi_slot;   // workspace slot of psi_s (store)
-  int gphi_slot;  // workspace slot of g_phi_s (post)
 };
 
 // Where a stage takes its inputs and puts its outputs: the block's shared
@@ -326,7 +324,7 @@ struct GmCtx {
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      if (g.store) __stcs(a.ws_psi + ((size_t)g.psi_slot * a.ws_n + il) * MM + at(li, i0 + q * di), x[q]);
+      if (g.store) __stcs(a.ws_psi + ((size_t)(g.s - 1) * a.ws_n + il) * MM + at(li, i0 + q * di), x[q]);
       x[q] = cmul(x[q], o[q]);
     }
   }
@@ -356,7 +354,7 @@ struct GmCtx {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const size_t e = at(li, i0 + q * di);
-      __stcs(a.ws_gphi + ((size_t)g.gphi_slot * a.ws_n + il) * MM + e, x[q]);
+      __stcs(a.ws_gphi + ((size_t)g.s * a.ws_n + il) * MM + e, x[q]);
       const float2 gv = cmulc(x[q], o[q]);
       if (g.s == 0)
         __stcs(a.ws_gp + (size_t)il * MM + e, gv);
@@ -665,16 +663,30 @@ struct GmLauncher {
   cudaStream_t st;
   int launches = 0;
 
-  cudaError_t line(int op, int cols, int s = 0, int pre = 0, int post = 0, int store = 0, int psi_slot = 0,
-                   int gphi_slot = 0) {
-    const GmLineArgs g{op, cols, s, pre, post, store, psi_slot, gphi_slot};
+  // The kernel keeps psi_s in ws_psi slot s - 1 and g_phi_s in ws_gphi slot
+  // s; another slot (recompute mode) is reached by shifting the launch's
+  // workspace pointers by whole slots, so the kernel's addressing (and its
+  // register budget) stays the same.
+  cudaError_t line(int op, int cols, int s = 0, int pre = 0, int post = 0, int store = 0, int psi_slot = -1,
+                   int gphi_slot = -1) {
+    const GmLineArgs g{op, cols, s, pre, post, store};
+    ChainArgs la = a;
+    const size_t slot_elems = (size_t)a.ws_n * M * M;
+    if (store && psi_slot >= 0)
+      la.ws_psi = reinterpret_cast<float2*>(reinterpret_cast<uintptr_t>(a.ws_psi) +
+                                            (uintptr_t)((int64_t)(psi_slot - (s - 1)) * (int64_t)slot_elems *
+                                                        (int64_t)sizeof(float2)));
+    if (post && gphi_slot >= 0)
+      la.ws_gphi = reinterpret_cast<float2*>(reinterpret_cast<uintptr_t>(a.ws_gphi) +
+                                             (uintptr_t)((int64_t)(gphi_slot - s) * (int64_t)slot_elems *
+                                                         (int64_t)sizeof(float2)));
     const unsigned grid = (unsigned)((size_t)a.n_pos * M / gm_lines(M));
     const size_t smem = gm_fft_smem_bytes(M);
     switch (M) {
-      case 96: k_gm_line<96><<<grid, GmTraits<96>::threads, smem, st>>>(a, wv, M, plan, g); break;
-      case 192: k_gm_line<192><<<grid, GmTraits<192>::threads, smem, st>>>(a, wv, M, plan, g); break;
-      case 256: k_gm_line<256><<<grid, GmTraits<256>::threads, smem, st>>>(a, wv, M, plan, g); break;
-      default: k_gm_line<0><<<grid, kGmThreads, smem, st>>>(a, wv, M, plan, g); break;
+      case 96: k_gm_line<96><<<grid, GmTraits<96>::threads, smem, st>>>(la, wv, M, plan, g); break;
+      case 192: k_gm_line<192><<<grid, GmTraits<192>::threads, smem, st>>>(la, wv, M, plan, g); break;
+      case 256: k_gm_line<256><<<grid, GmTraits<256>::threads, smem, st>>>(la, wv, M, plan, g); break;
+      default: k_gm_line<0><<<grid, kGmThreads, smem, st>>>(la, wv, M, plan, g); break;
     }
     ++launches;
     return cudaGetLastError();
