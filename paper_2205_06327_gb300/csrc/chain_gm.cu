@@ -236,7 +236,11 @@ struct GmTraits<192> {
 };
 
 // Lines per block: the largest divisor of M with L M <= PTYCHO_GM_ELEMS.
+#ifndef PTYCHO_GM192_LINES
+#define PTYCHO_GM192_LINES 0
+#endif
 __host__ __device__ constexpr int gm_lines(int M) {
+  if (M == 192 && PTYCHO_GM192_LINES > 0) return PTYCHO_GM192_LINES;
   int best = 1;
   for (int L = 1; L <= M && L * M <= PTYCHO_GM_ELEMS; ++L)
     if (M % L == 0) best = L;

@@ -66,6 +66,10 @@ def test_version_and_parameter_validation(lib):
     assert lib.ptycho_loss_grad_host(None, None, None, None, None, None, None, None, None) == PTYCHO_ERR_ARG
     assert b"plan is NULL" in lib.ptycho_last_error()
     assert lib.ptycho_multi_loss_grad(None, -1, None) == PTYCHO_ERR_ARG
+    assert lib.ptycho_multi_step(None, 0, float("nan"), 0.0, None) == PTYCHO_ERR_ARG
+    assert b"finite" in lib.ptycho_last_error()
+    assert lib.ptycho_step_accumulate(None, None, None, None, None, 1e-3, 0.0, None, 1, None, None) == PTYCHO_ERR_ARG
+    assert b"plan is NULL" in lib.ptycho_last_error()
     assert lib.ptycho_plan_destroy(None) == PTYCHO_ERR_ARG
 
 
