@@ -203,7 +203,9 @@ constexpr int kGmThreads = PTYCHO_GM_THREADS;
 // 128-register budget (2 blocks/SM) win for 256 (197 vs 215 ms); 96 takes the
 // large radices at 80 registers (39 vs 42 ms); 192 keeps radix 8 at 64
 // registers and 256 threads (368 ms against 385-405 ms with radix 12/16,
-// and 378-402 ms with 192, 384 or 512 threads per block).
+// and 378-402 ms with 192, 384 or 512 threads per block; 16 lines per block
+// against 32 or 64: 406 against 468 and 581 ms for the 192 problems alone).
+// The paper's 1024 window takes radices 16 16 4 at 128 registers.
 #ifndef PTYCHO_GM192_THREADS
 #define PTYCHO_GM192_THREADS 256
 #endif
@@ -226,6 +228,12 @@ template <>
 struct GmTraits<96> {
   static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16;
   static constexpr int min_blocks = 3;
+  static constexpr int threads = kGmThreads;
+};
+template <>
+struct GmTraits<1024> {  // the paper's detector size (Table I): radices 16 16 4
+  static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16;
+  static constexpr int min_blocks = 2;
   static constexpr int threads = kGmThreads;
 };
 template <>
@@ -654,6 +662,7 @@ cudaError_t gm_prepare(int) {
   if ((e = gm_set_smem<0>((int)most)) != cudaSuccess) return e;
   if ((e = gm_set_smem<96>((int)gm_fft_smem_bytes(96))) != cudaSuccess) return e;
   if ((e = gm_set_smem<192>((int)gm_fft_smem_bytes(192))) != cudaSuccess) return e;
+  if ((e = gm_set_smem<1024>((int)gm_fft_smem_bytes(1024))) != cudaSuccess) return e;
   return gm_set_smem<256>((int)gm_fft_smem_bytes(256));
 }
 
@@ -690,6 +699,7 @@ struct GmLauncher {
       case 96: k_gm_line<96><<<grid, GmTraits<96>::threads, smem, st>>>(la, wv, M, plan, g); break;
       case 192: k_gm_line<192><<<grid, GmTraits<192>::threads, smem, st>>>(la, wv, M, plan, g); break;
       case 256: k_gm_line<256><<<grid, GmTraits<256>::threads, smem, st>>>(la, wv, M, plan, g); break;
+      case 1024: k_gm_line<1024><<<grid, GmTraits<1024>::threads, smem, st>>>(la, wv, M, plan, g); break;
       default: k_gm_line<0><<<grid, kGmThreads, smem, st>>>(la, wv, M, plan, g); break;
     }
     ++launches;
