@@ -382,3 +382,54 @@ def test_delayed_accumulation_convergence_by_period(dev):
     for T, F in curves.items():
         print(f"T = {T:3d}: F per epoch " + " ".join(f"{f:.6e}" for f in F))
         assert all(b < a for a, b in zip(F, F[1:])), (T, F)
+
+
+@pytest.mark.parametrize("T", [1, 3])
+def test_delayed_accumulation_matches_the_host_ranks_schedule(dev, T):
+    """The GPU's Algorithm 1 (SequentialGD with period T, one tile) against the
+    host-rank implementation of the same schedule (halo_passes.appp_epoch on a
+    one-tile grid in a one-rank gloo group, with the FP64 oracle's
+    per-location gradients): two implementations of the algorithm, one epoch,
+    the object's iterates to 1e-6."""
+    import os
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_2205_06327_gb300 import api
+    from paper_2205_06327_gb300 import halo_passes as hp
+    from paper_2205_06327_gb300.sgd import SequentialGD
+    wl = synth.workload_random(64, 2, 2, 3, 9, seed=93, amp_jitter=0.1)
+    I = (measurements(wl) * 1.1).astype(np.float32)
+    obj0 = c64(start_object(wl, "perturbed", 7))
+    P, h, a = c64(wl.probe), propagator(wl), 3e-3
+    g = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
+    sgd = SequentialGD(g, 1, dev, period=T)
+    O = to_dev(obj0, torch.complex64, dev)
+    sgd.epoch(to_dev(wl.pos, torch.int32, dev), to_dev(wl.probe, torch.complex64, dev), O,
+              to_dev(I, torch.float32, dev), a, 0.0)
+    torch.cuda.synchronize()
+    sgd.close()
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        grid = hp.tile_grid(wl.H, wl.W, 1, 1, wl.pos, wl.M)
+        me = grid[0][0]
+        e = me.ext
+        assert (e.y0, e.x0, e.y1, e.x1) == (0, 0, wl.H, wl.W)
+
+        def grad_fn(i, tile):
+            _, gOi, _ = orc.position_loss_grad(P, tile.numpy(), wl.pos[i], I[i].astype(np.float64), h)
+            gr = torch.zeros_like(tile)
+            y, x = int(wl.pos[i][0]), int(wl.pos[i][1])
+            gr[:, y:y + wl.M, x:x + wl.M] = torch.from_numpy(gOi)
+            return gr
+
+        tile = torch.from_numpy(obj0.copy())
+        hp.appp_epoch(tile, torch.zeros_like(tile), grid, me, np.arange(wl.N), grad_fn, a, T)
+    finally:
+        dist.destroy_process_group()
+    assert rel_l2(O.cpu().numpy(), tile.numpy()) <= 1e-6
