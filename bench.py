@@ -283,13 +283,32 @@ CHAIN_SOURCES = {"fp32": ("chain_kernels.cu", "chain_body.inc", "fft2d.cuh"), "b
                  "fp16x3": ("chain_tc.cu", "tc_bf16.cuh")}
 
 
-def chain_source_hash(precision: str) -> str:
+# every kernel of one evaluation: the chain, the reductions, and the host code that launches them
+STEP_SOURCES = {p: CHAIN_SOURCES[p] + ("reduce_kernels.cu", "ptycho_api.cu") for p in CHAIN_SOURCES}
+
+
+def chain_source_hash(precision: str, names=None) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in CHAIN_SOURCES[precision]:
+    for name in (names or CHAIN_SOURCES[precision]):
         with open(os.path.join(ROOT, "paper_2205_06327_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def measured_step_traffic_per_position(precision: str, M: int, S: int):
+    """DRAM bytes per position of a whole evaluation (every kernel of one step,
+    ncu, profiles/traffic.json), or None if any of those sources changed."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"step_{precision}_M{M}_S{S}")
+    if not e or e.get("source_hash") != chain_source_hash(precision, STEP_SOURCES[precision]):
+        return None
+    return float(e["dram_bytes_per_position"])
 
 
 def measured_traffic_per_position(precision: str, M: int, S: int):
@@ -500,6 +519,20 @@ def measure_workload(wl, config_id, args, device, world, rank, local, ckpt_every
     return meas
 
 
+def step_traffic(wl, args):
+    """DRAM bytes per position of a whole evaluation against the method's
+    algorithmic bytes (intensities, object, object gradient once each)."""
+    if args.ckpt_every or args.positions or args.order != "raster":
+        return None
+    b = measured_step_traffic_per_position(args.precision, wl.M, wl.S)
+    if b is None:
+        return None
+    alg = hbm_bytes_per_evaluation(wl) / wl.N
+    return {"dram_bytes_per_position": b, "algorithmic_bytes_per_position": alg, "ratio": b / alg,
+            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every kernel of one "
+                      "evaluation (profiles/traffic.json)"}
+
+
 def parity_sample(wl, args, device, tile, ckpt_every, tensors, pool, k=48):
     """Relative errors of the timed path against the FP64 oracle on k positions
     spread over the scan (outside the timed region): the same kernels, launch
@@ -631,6 +664,7 @@ def run_gpu(args, world, rank, local, pool):
         "roofline": m["roofline"],
         "hbm_kernels": m["hbm_kernels"],
         "path_bound_ms": m["path_bound_ms"],
+        "step_traffic": step_traffic(wl, args),
         "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
         "gpu_launches": int(round(m["launches_per_step"] * args.steps)),
         "gpu_launches_per_step": m["launches_per_step"],
