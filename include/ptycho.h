@@ -228,7 +228,8 @@ PTYCHO_API int ptycho_step(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* 
  * second update, O <- O - alpha_obj acc, and clears it.  On one GPU the
  * whole object is one tile, so the passes that would add the neighbouring
  * tiles' buffers before the second update have nothing to add.
- *   acc        c64 [S][H][W] device, caller-owned, updated in place
+ *   acc        c64 [S][H][W] device, caller-owned, updated in place; it must
+ *              not overlap obj or probe
  *   loss_out   double[1] device or host, or NULL: F (these positions) before the update
  * The paper updates only V; pass alpha_probe = 0 to keep the probe fixed. */
 PTYCHO_API int ptycho_step_accumulate(ptycho_plan plan, const int32_t* pos_yx, ptycho_c64* probe,

@@ -183,7 +183,8 @@ cudaError_t launch_chain(int M, ChainMode mode, const ChainArgs& a, cudaStream_t
 }
 
 cudaError_t launch_chain_multi(int M, const MultiChainArgs& m, cudaStream_t st) {
-  if (m.n <= 0 || m.n > kMultiChainMax || m.start[m.n] <= 0) return cudaSuccess;
+  if (m.n < 0 || m.n > kMultiChainMax) return cudaErrorInvalidValue;
+  if (m.n == 0 || m.start[m.n] <= 0) return cudaSuccess;
   const dim3 grid(m.start[m.n]), block(chain_threads(M));
   const size_t smem = chain_smem_bytes(M);
   if (M == 128)

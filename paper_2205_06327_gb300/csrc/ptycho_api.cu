@@ -1179,7 +1179,7 @@ int ptycho_multi_loss_grad(const ptycho_problem* problems, int32_t n, void* stre
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<int> fused;
   int rc = run_multi(problems, n, [&](const ptycho_problem& q) {
-    if (fusable(q.plan)) {
+    if (fusable(q.plan) && (q.grad_obj || q.grad_probe)) {  // loss-only problems take the cheaper chain
       fused.push_back((int)(&q - problems));
       return PTYCHO_OK;
     }
