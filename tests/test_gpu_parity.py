@@ -344,7 +344,7 @@ def test_potential_parameterisation(dev):
     assert abs(float(np.sum(Vt.grad.cpu().numpy() * d)) - fd) <= 1e-4 * abs(fd)
 
 
-@pytest.mark.parametrize("M,S,L", [(64, 7, 3), (128, 5, 2), (64, 4, 1)])
+@pytest.mark.parametrize("M,S,L", [(64, 7, 3), (128, 5, 2), (64, 4, 1), (128, 4, 3), (64, 6, 5)])
 def test_recompute_mode_matches_store_all(dev, M, S, L):
     """Checkpoint every L slices + per-segment recomputation: the loss is
     bit-identical (same forward), the gradients agree with the store-all mode
@@ -389,6 +389,27 @@ def test_recompute_workspace_does_not_hold_a_patch_per_slice(dev, M):
         assert full.workspace_bytes // 4 == 2 * S * per + 8
         auto.close()
         full.close()
+
+
+@pytest.mark.parametrize("M", [64, 128, 96])
+def test_recompute_mode_over_several_chunks(dev, M):
+    """Recompute mode with a workspace that holds only a few positions: every
+    chunk runs its K launches and per-segment accumulations (the later chunks
+    adding to the gradient), and the results equal the store-all mode over one
+    chunk to FP32 reassociation."""
+    S, L = 5, 2
+    wl = synth.workload_random(M, S, 3, 3, 11, seed=44 + M, amp_jitter=0.1)
+    I = (measurements(wl) * 1.2).astype(np.float32)
+    obj = start_object(wl, "perturbed", 9)
+    K = -(-S // L)
+    per = (K + L - 1 + (L + 1 if M not in (64, 128) else 0)) * M * M * 8 + M * M * 8 + 8
+    small = _plan(wl, dev, ckpt_every=L, workspace_bytes=3 * per)
+    assert small.chunk == 3
+    small.close()
+    ref = _run(wl, obj, I, dev)
+    rc = _check(wl, obj, I, dev, ckpt_every=L, workspace_bytes=3 * per)
+    assert abs(rc[0] - ref[0]) <= 1e-6 * abs(ref[0])
+    assert rel_l2(rc[1], ref[1]) <= 2e-6 and rel_l2(rc[2], ref[2]) <= 2e-6
 
 
 @pytest.mark.parametrize("M,S,L", [(96, 7, 3), (48, 5, 2), (192, 4, 1)])
