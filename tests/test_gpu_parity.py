@@ -582,6 +582,29 @@ def test_generic_windows(dev, M, S, ny, nx, step):
     _check(wl, start_object(wl, "perturbed", 4), I, dev)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_generic_windows_random_shapes(dev, seed):
+    """Seeded random windows 2^a 3^b in [12, 324] on the runtime radix
+    schedule and the compiled instances (radix mixes of 8, 4, 2, 3), random
+    slice counts, rasters and step sizes, every wave kept or recomputed."""
+    g = synth.rng(7000 + seed)
+    M = int(g.choice([M for M in range(12, 325) if M not in (64, 128) and _smooth(M)]))
+    S = int(g.integers(1, 5))
+    ny, nx = int(g.integers(1, 4)), int(g.integers(1, 4))
+    step = int(g.integers(1, max(2, M // 3)))
+    L = int(g.integers(0, S)) if S > 1 else 0
+    wl = synth.workload_random(M, S, ny, nx, step, seed=7100 + seed, amp_jitter=0.1)
+    I = (measurements(wl) * 1.15).astype(np.float32)
+    _check(wl, start_object(wl, "perturbed", seed), I, dev, ckpt_every=L)
+
+
+def _smooth(M):
+    for p in (2, 3):
+        while M % p == 0:
+            M //= p
+    return M == 1
+
+
 @pytest.mark.parametrize("M,S,ny,nx,step", [(8, 2, 2, 2, 3), (81, 2, 2, 2, 9)])
 def test_generic_window_extremes(dev, M, S, ny, nx, step):
     """The smallest window (one radix-8 stage: the first stage reads and the last
