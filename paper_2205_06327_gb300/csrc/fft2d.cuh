@@ -193,13 +193,8 @@ struct PassShape {
 // Launder a value through an empty asm so index arithmetic derived from it
 // is recomputed where it is used instead of being hoisted out of the slice
 // loop and pinned in registers.
-#ifndef PTYCHO_OPAQUE_INDEX
-#define PTYCHO_OPAQUE_INDEX 1
-#endif
 __device__ __forceinline__ int opaque(int x) {
-#if PTYCHO_OPAQUE_INDEX
   asm volatile("" : "+r"(x));
-#endif
   return x;
 }
 
