@@ -392,7 +392,7 @@ def measure_workload(wl, config_id, args, device, world, rank, local, ckpt_every
 
     obj0 = start_object(wl)
     geom = api.Geometry(wl.M, wl.S, wl.H, wl.W, wl.N, wl.lambda_A, wl.dz_A, wl.pixel_A)
-    tile = (0, 0)
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else (0, 0)
     ws = int(args.workspace_mb) << 20
     plan = api.Plan(geom, device, async_check=True, timing=True, tile=tile, ckpt_every=ckpt_every,
                     precision=args.precision, workspace_bytes=ws)
@@ -407,7 +407,7 @@ def measure_workload(wl, config_id, args, device, world, rank, local, ckpt_every
         gen = torch.Generator(device=device)
         gen.manual_seed(1000 + config_id)
         I = torch.poisson(I, generator=gen)
-    if config_id == 3:
+    if config_id == 3 and not args.tile:
         # The gradient is accumulated per tile; the tile shape only changes the
         # speed (results are bit-identical), so the 8 x 8 tessellation of the
         # workload competes with smaller tiles and the fastest is kept.
@@ -799,6 +799,9 @@ def main(argv=None):
                          "(the library uses the caller's order; this measures what the order costs)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "fp16x3"],
                     help="bf16x3 / fp16x3: 2-D transforms as hi/lo split DFT products on the tensor cores")
+    ap.add_argument("--tile", default="",
+                    help="object-gradient accumulation tile HxW (e.g. 16x64; default: the library's, "
+                         "tuned for workload 3)")
     ap.add_argument("--workspace-mb", type=int, default=0,
                     help="cap on the plan's workspace in MiB (0: the library's default, 8 GiB); the "
                          "positions run in chunks that fit it")
