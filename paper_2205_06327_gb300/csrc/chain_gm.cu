@@ -230,10 +230,16 @@ struct GmTraits<96> {
   static constexpr int min_blocks = 3;
   static constexpr int threads = kGmThreads;
 };
+#ifndef PTYCHO_GM1024_BIG
+#define PTYCHO_GM1024_BIG 1
+#endif
+#ifndef PTYCHO_GM1024_MIN_BLOCKS
+#define PTYCHO_GM1024_MIN_BLOCKS 2
+#endif
 template <>
 struct GmTraits<1024> {  // the paper's detector size (Table I): radices 16 16 4
-  static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16;
-  static constexpr int min_blocks = 2;
+  static constexpr bool big = PTYCHO_GM_MAX_RADIX >= 16 && PTYCHO_GM1024_BIG;
+  static constexpr int min_blocks = PTYCHO_GM1024_MIN_BLOCKS;
   static constexpr int threads = kGmThreads;
 };
 template <>
@@ -247,8 +253,12 @@ struct GmTraits<192> {
 #ifndef PTYCHO_GM192_LINES
 #define PTYCHO_GM192_LINES 0
 #endif
+#ifndef PTYCHO_GM1024_LINES
+#define PTYCHO_GM1024_LINES 0
+#endif
 __host__ __device__ constexpr int gm_lines(int M) {
   if (M == 192 && PTYCHO_GM192_LINES > 0) return PTYCHO_GM192_LINES;
+  if (M == 1024 && PTYCHO_GM1024_LINES > 0) return PTYCHO_GM1024_LINES;
   int best = 1;
   for (int L = 1; L <= M && L * M <= PTYCHO_GM_ELEMS; ++L)
     if (M % L == 0) best = L;
