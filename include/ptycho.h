@@ -241,13 +241,17 @@ PTYCHO_API int ptycho_step_accumulate(ptycho_plan plan, const int32_t* pos_yx, p
  * problems of different windows, slice counts and sizes).  Each problem has
  * its own plan and arrays, as for the single-problem calls; two entries may
  * not share a plan, and problems must not share output arrays.  The
- * problems' work is enqueued on `stream` in order, so one call can be
- * captured in one CUDA graph when every plan uses PTYCHO_FLAG_ASYNC_CHECK.
- * The call never synchronises: loss_out must be a device pointer or NULL.
- * Results are bit-identical to the single-problem calls.  On an error the
- * message names the problem; the work of the problems before it stays
- * enqueued.  The paper has no counterpart: it reconstructs one dataset at a
- * time. */
+ * problems' work is enqueued on `stream`, so one call can be captured in one
+ * CUDA graph when every plan uses PTYCHO_FLAG_ASYNC_CHECK: first, in order,
+ * the problems the register-resident kernels do not take; then the FP32
+ * problems with M = 64 or 128 that keep every wave, grouped by window, whose
+ * chains of chunk r run in one launch per group (up to 16 problems per
+ * launch), each followed by that problem's reductions of the chunk.  The
+ * call never synchronises (unless a plan lacks PTYCHO_FLAG_ASYNC_CHECK):
+ * loss_out must be a device pointer or NULL.  Results are bit-identical to
+ * the single-problem calls.  On an error the message names the problem; the
+ * work enqueued before it stays enqueued.  The paper has no counterpart: it
+ * reconstructs one dataset at a time. */
 typedef struct {
   ptycho_plan plan;
   const int32_t* pos_yx;   /* [N][2] device */
