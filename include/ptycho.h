@@ -126,8 +126,11 @@ typedef struct {
                          segment is rebuilt.  With K = ceil(S / L) segments
                          the workspace per position holds K + L wave-sized
                          buffers (K - 2 checkpoints, one segment, the parked
-                         adjoint state, the probe gradient) instead of 2S,
-                         for (K - 1)(L - 1) extra propagations.  L = 0 is
+                         adjoint state, the probe gradient) instead of 2S
+                         (the generic-window path: K + 2L + 1, the segment's
+                         exit-wave gradients and the chunk's wave buffer
+                         besides), for (K - 1)(L - 1) extra propagations.
+                         L = 0 is
                          used when L >= S.  PTYCHO_CKPT_AUTO: K =
                          ceil(sqrt(S)), L = ceil(S / K): about 2 sqrt(S)
                          buffers.  Applies to the FP32 path (every window);
