@@ -205,7 +205,9 @@ constexpr int kGmThreads = PTYCHO_GM_THREADS;
 // registers and 256 threads (368 ms against 385-405 ms with radix 12/16,
 // and 378-402 ms with 192, 384 or 512 threads per block; 16 lines per block
 // against 32 or 64: 406 against 468 and 581 ms for the 192 problems alone).
-// The paper's 1024 window takes radices 16 16 4 at 128 registers.
+// The paper's 1024 window takes radices 16 16 4 at 128 registers and 4 lines
+// per block (143 positions/s at 100 slices, against 117 with radix 8 at 64
+// registers, 131 and 140 with 2 and 8 lines per block).
 #ifndef PTYCHO_GM192_THREADS
 #define PTYCHO_GM192_THREADS 256
 #endif
