@@ -653,7 +653,8 @@ def run_gpu(args, world, rank, local, pool):
     csum = m["csum"]
     line = {
         "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": m["t_max"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": m["t_max"] * 1e3,
+        "ms_per_step_median": float(np.median(m["step_ms"])), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32", "fp16x3": "f16x3+f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": wl.name, "positions": wl.N, "M": wl.M, "S": wl.S, "object": [wl.H, wl.W],
